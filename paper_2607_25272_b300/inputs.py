@@ -1,0 +1,79 @@
+"""Seeded synthetic least-squares problems Y = X beta + zeta (Eq. model).
+
+This module generates inputs only; it holds none of SPCG's arithmetic.  It is
+the one module that both the CUDA path's tests/bench and the CPU oracle's
+tests read their inputs from.  Every generator is a pure function of its
+arguments (numpy PCG64 streams), FP64 on the host.
+
+Problem families:
+* ``gaussian_problem``   - X_ij iid N(0,1), beta iid N(0,1), zeta iid N(0, sigma^2).
+* ``svd_problem``        - X = U diag(s) V^T with U a random N x d orthonormal
+  basis (CholeskyQR2 of a Gaussian matrix, optionally with rows scaled by
+  |Student-t(df)| before orthonormalising, which gives heavy-tailed leverage
+  scores while keeping kappa(X) exact), V a random d x d orthogonal matrix and
+  s geometric from 1 to 1/kappa.
+* ``paper_problem``      - the experimental design of Sec. 4: X = G diag(s~),
+  s~ geometric from 1 to 1/kappa, beta iid N(0,1), zeta iid N(0, sigma^2).
+* ``scaled_columns_problem`` - X_ij iid N(0,1) times per-column scales
+  log-uniform in [lo, hi] (the batched workload).
+"""
+import numpy as np
+
+
+def _response(X, beta, zeta):
+    # Row sums without BLAS so that Y does not depend on the BLAS kernel.
+    return (X * beta[None, :]).sum(axis=1) + zeta
+
+
+def gaussian_problem(N, d, sigma=1.0, seed=1):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((N, d))
+    beta = rng.standard_normal(d)
+    zeta = sigma * rng.standard_normal(N)
+    return X, _response(X, beta, zeta), beta
+
+
+def orthonormal_basis(G):
+    """CholeskyQR2: two rounds of G <- G chol(G^T G)^{-T}."""
+    Q = np.array(G, dtype=np.float64, copy=True)
+    for _ in range(2):
+        L = np.linalg.cholesky(Q.T @ Q)
+        # Q <- Q L^{-T}: solve L Q^T = Q^T column block by column block.
+        Q = np.linalg.solve(L, Q.T).T
+    return np.ascontiguousarray(Q)
+
+
+def svd_problem(N, d, kappa, sigma, seed=1, leverage_df=None):
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((N, d))
+    if leverage_df is not None:
+        w = np.abs(rng.standard_t(leverage_df, size=N))
+        G *= w[:, None]
+    U = orthonormal_basis(G)
+    del G
+    V, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    s = kappa ** (-np.arange(d) / max(d - 1, 1))
+    U *= s[None, :]
+    X = np.ascontiguousarray(U @ V.T)
+    del U
+    beta = rng.standard_normal(d)
+    zeta = sigma * rng.standard_normal(N)
+    return X, _response(X, beta, zeta), beta
+
+
+def paper_problem(N, d, kappa, sigma2, seed=1):
+    rng = np.random.default_rng(seed)
+    s = kappa ** (-np.arange(d) / max(d - 1, 1))
+    X = rng.standard_normal((N, d)) * s[None, :]
+    beta = rng.standard_normal(d)
+    zeta = np.sqrt(sigma2) * rng.standard_normal(N)
+    return X, _response(X, beta, zeta), beta
+
+
+def scaled_columns_problem(N, d, lo, hi, sigma, seed=1):
+    rng = np.random.default_rng(seed)
+    c = 10.0 ** rng.uniform(np.log10(lo), np.log10(hi), size=d)
+    X = rng.standard_normal((N, d)) * c[None, :]
+    beta = rng.standard_normal(d)
+    zeta = sigma * rng.standard_normal(N)
+    return X, _response(X, beta, zeta), beta

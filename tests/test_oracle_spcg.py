@@ -1,0 +1,174 @@
+"""Pins for the oracle's PCG and SPCG (Sec. 2.2, Algorithm 1, Sec. 3, Sec. 4)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle.linalg import ols, r_factor
+from oracle.metrics import delta_t, rel_pred_error
+from oracle.spcg import (default_schedule, full_pcg, pcg, sketch_all, spcg,
+                         thm33_bound)
+from oracle.srht import nested_sketches, srht_transform
+from paper_2607_25272_b300.inputs import (gaussian_problem, paper_problem,
+                                          svd_problem)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_default_schedule_values():
+    s = default_schedule(20000, 50)
+    assert s["n_pad"] == 32768 and s["r"] == 300
+    assert s["m"] == [512, 1024, 2048, 4096, 8192, 16384] and s["a"] == [3] * 6
+    s = default_schedule(1 << 20, 500)
+    assert s["m"] == [1 << k for k in range(12, 20)] and s["r"] == 3000
+    s = default_schedule(1 << 17, 64)
+    assert s["m"][0] == 512 and s["m"][-1] == 1 << 16 and len(s["m"]) == 8
+    # every schedule satisfies d < r < m_1 < ... < m_K < N (Sec. 2.2)
+    for N, d in [(20000, 50), (1 << 20, 500), (1 << 22, 1000), (5000, 1)]:
+        s = default_schedule(N, d)
+        ms = s["m"]
+        assert all(a < b for a, b in zip(ms, ms[1:]))
+        if ms:
+            assert d < s["r"] < ms[0] and ms[-1] < N
+
+
+def test_theorem_3_3_bounds_fig1a_facts():
+    # Fig. 1a discussion (Sec. 4.1): N = 2^20, d = 2^6; the unrounded
+    # bounds for a_2 and a_K nearly coincide, decrease in omega and stay
+    # below three on omega in {2^-4, ..., 1}.
+    d, N = 64, 1 << 20
+    s = default_schedule(N, d)
+    ms = s["m"]
+    omegas = [2.0**-k for k in range(4, -1, -1)]
+    a2 = [thm33_bound(ms[0], ms[1], d, w) for w in omegas]
+    aK = [thm33_bound(ms[-2], ms[-1], d, w) for w in omegas]
+    assert all(x < 3 for x in a2 + aK)
+    assert all(x > y for x, y in zip(a2, a2[1:]))
+    assert all(abs(x - y) < 0.05 for x, y in zip(a2, aK))
+    assert all(x >= y for x, y in zip(a2, aK))
+    # closed form at omega = 1 with r_{1,2}^2 = 2 + d/(m_1 - d) = 15/7
+    assert math.isclose(a2[-1], math.log(2 * math.sqrt(15 / 7) + 1) / math.log(4), rel_tol=1e-14)
+
+
+@pytest.mark.parametrize("d,kappa", [(1, 1.0), (3, 5.0), (8, 10.0)])
+def test_pcg_terminates_within_d_iterations(d, kappa):
+    A, b, _ = svd_problem(200, d, kappa, 1.0, seed=d)
+    # In exact arithmetic CG stops at step d.  In FP64 the d-th iterate carries
+    # the rounding of d steps amplified by kappa (measured ~4e-10 here; the
+    # same recurrence in 80-bit arithmetic gives ~1e-13), so the pin is the
+    # collapse of the error at step d, not an exact zero.
+    rng = np.random.default_rng(d)
+    R = np.eye(d) + 0.1 * np.triu(rng.uniform(-1, 1, (d, d)), 1)
+    bh = ols(A, b)
+    for Rp in (np.eye(d), R):
+        beta, _ = pcg(A, b, Rp, np.zeros(d), d)
+        assert rel_pred_error(A, beta, bh) < 1e-8
+        beta2, _ = pcg(A, b, Rp, np.zeros(d), d + 1)
+        assert rel_pred_error(A, beta2, bh) < 1e-11
+        if d > 1:   # d - 1 steps: the Krylov space is one dimension short
+            beta1, _ = pcg(A, b, Rp, np.zeros(d), d - 1)
+            assert rel_pred_error(A, beta1, bh) > 1e-4
+
+
+def test_exact_preconditioner_converges_in_one_iteration():
+    A, b, _ = svd_problem(500, 10, 1e5, 0.2, seed=2)
+    beta, _ = pcg(A, b, r_factor(A), np.zeros(10), 1)
+    assert rel_pred_error(A, beta, ols(A, b)) < 1e-9
+
+
+def test_lemma_a2_cg_bound_each_iterate():
+    # ||B(x_j - x*)|| <= 2 ((sqrt k - 1)/(sqrt k + 1))^j ||B(x_0 - x*)|| for
+    # B = A R^{-1} (PCG on A = CG on B), kappa = kappa(B^T B) exactly.
+    A, b, _ = svd_problem(3000, 20, 1e3, 0.5, seed=4)
+    R = r_factor(np.random.default_rng(0).standard_normal((400, 20)) @ np.diag(np.geomspace(1, 1e-3, 20)))
+    B = np.linalg.solve(R.T, A.T).T
+    kappa = np.linalg.cond(B.T @ B)
+    q = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+    x_star = ols(A, b)
+    e0 = np.linalg.norm(A @ x_star)
+    iterates = []
+    pcg(A, b, R, np.zeros(20), 15, callback=lambda bt: iterates.append(bt.copy()))
+    for j, bt in enumerate(iterates, start=1):
+        assert np.linalg.norm(A @ (bt - x_star)) <= 2 * q**j * e0 * (1 + 1e-9) + 1e-12
+
+
+def _embedding_eps(N, d, X, seed, schedule):
+    """epsilon = max over S_1..S_K, S-hat of ||U^T S^T S U - I|| for U = orth(X)."""
+    U, _ = np.linalg.qr(X)
+    ZU, ZY = srht_transform(U, np.zeros(N), seed)
+    stages, U_hat = nested_sketches(ZU, ZY, schedule["m"], schedule["r"], seed)
+    eps = [np.linalg.norm(A.T @ A - np.eye(d), 2) for A, _ in stages]
+    eps_hat = np.linalg.norm(U_hat.T @ U_hat - np.eye(d), 2)
+    return max(eps + [eps_hat]), eps, eps_hat
+
+
+def test_stage_contraction_and_lemma_a4_with_measured_epsilon():
+    # Eq. (app-stage-intermediate) and Lemma A.4 hold deterministically given
+    # the measured distortion epsilon < 1.
+    N, d = 1 << 13, 8
+    X, Y, _ = svd_problem(N, d, 1e3, 0.5, seed=12)
+    sched = {"m": [256, 512, 1024, 2048, 4096], "a": [2, 2, 2, 2, 2], "r": 128}
+    seed = 77
+    eps, eps_i, eps_hat = _embedding_eps(N, d, X, seed, sched)
+    assert eps < 1
+    stages, A_hat, R = sketch_all(X, Y, seed, sched)
+    H = R.T @ R
+    w, V = np.linalg.eigh(H)
+    H_mhalf = V @ np.diag(w ** -0.5) @ V.T
+    full = np.linalg.eigvalsh(H_mhalf @ X.T @ X @ H_mhalf)
+    assert full.min() >= 1 / (1 + eps_hat) - 1e-10 and full.max() <= 1 / (1 - eps_hat) + 1e-10
+    beta = np.zeros(d)
+    for (A_i, b_i), a_i, e_i in zip(stages, sched["a"], eps_i):
+        e = max(e_i, eps_hat)
+        lam = np.linalg.eigvalsh(H_mhalf @ A_i.T @ A_i @ H_mhalf)
+        assert lam.min() >= (1 - e) / (1 + e) - 1e-10 and lam.max() <= (1 + e) / (1 - e) + 1e-10
+        tilde = ols(A_i, b_i)
+        before = np.linalg.norm(X @ (beta - tilde))
+        beta, _ = pcg(A_i, b_i, R, beta, a_i)
+        after = np.linalg.norm(X @ (beta - tilde))
+        assert after <= 2 * math.sqrt((1 + e) / (1 - e)) * e**a_i * before * (1 + 1e-9) + 1e-12
+
+
+def test_full_sampling_spcg_is_exact_after_one_iteration():
+    # m = N' and I-hat = all rows: S^T S = I, so the sketched solution is
+    # beta-hat, H-hat = X^T X and one PCG iteration reaches it.
+    X, Y, _ = svd_problem(1024, 6, 1e4, 0.1, seed=5)
+    sched = {"m": [1024], "a": [1], "r": 1024}
+    out = spcg(X, Y, seed=3, schedule=sched, tol=1e-10)
+    bh = ols(X, Y)
+    assert rel_pred_error(X, out["stage_betas"][0], bh) < 1e-9
+    assert out["refine_iters"] <= 1
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_stopping_rule_meets_tolerance(tol):
+    for seed, (X, Y, _) in enumerate([gaussian_problem(20000, 50, 1.0, seed=1),
+                                      svd_problem(16384, 40, 1e6, 0.1, seed=2)]):
+        out = spcg(X, Y, seed=seed + 1, tol=tol)
+        assert out["converged"]
+        assert rel_pred_error(X, out["beta"], ols(X, Y)) <= tol
+
+
+def test_theorem_3_2_reaches_ols_level():
+    # Delta_T -> Delta_OLS (Theorem 3.2 and Fig. 2a: SPCG reaches the OLS error)
+    X, Y, beta = paper_problem(1 << 15, 32, 1e4, 1e-8, seed=4)
+    out = spcg(X, Y, seed=9, tol=1e-8)
+    d_ols = delta_t(X, ols(X, Y), beta)
+    assert abs(delta_t(X, out["beta"], beta) - d_ols) <= 1e-3 * d_ols
+
+
+def test_table1_spcg_iterations_loose_band():
+    # Table 1 (N = 2^17, d = 64, kappa = 1e4): SPCG needs 25 iterations to the
+    # OLS target.  Reading: IT = first t with Delta_t <= 1.05 Delta_OLS.
+    # Band: +-4 (the paper averages 10 runs of an unstated implementation).
+    row = json.load(open(os.path.join(HERE, "golden", "table1_spcg.json")))["rows"][0]
+    its = []
+    for seed in (1, 2, 3):
+        X, Y, beta = paper_problem(row["N"], 64, row["kappa"], 1e-8, seed=seed)
+        d_ols = delta_t(X, ols(X, Y), beta)
+        hist = []
+        spcg(X, Y, seed=seed, tol=1e-9, callback=lambda b: hist.append(delta_t(X, b, beta)))
+        its.append(next(i + 1 for i, h in enumerate(hist) if h <= 1.05 * d_ols))
+    assert abs(np.mean(its) - row["SPCG_IT"]) <= 4
