@@ -1,0 +1,509 @@
+// The C ABI of include/spcg.h: context, Algorithm 1 orchestration, exports.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace spcg {
+
+spcg_status from_cuda(cudaError_t e) {
+  (void)cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? SPCG_E_OOM : SPCG_E_CUDA;
+}
+
+template <typename T>
+static spcg_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  SPCG_CK(cudaMalloc((void**)p, count * sizeof(T)));
+  return SPCG_OK;
+}
+
+template <typename T>
+static void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+static int64_t next_pow2(int64_t n) {
+  int64_t p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+static int ilog2(int64_t p) {
+  int k = 0;
+  while ((int64_t(1) << k) < p) ++k;
+  return k;
+}
+
+static spcg_status validate_schedule(const spcg_schedule& s, int64_t N, int d) {
+  const int64_t n_pad = next_pow2(N);
+  if (s.K < 0 || s.K > SPCG_MAX_STAGES) return SPCG_E_INVALID_ARG;
+  if (s.r < d || s.r > n_pad) return SPCG_E_INVALID_ARG;
+  for (int i = 0; i < s.K; ++i) {
+    if (s.m[i] < d || s.m[i] > n_pad || s.a[i] < 0) return SPCG_E_INVALID_ARG;
+    if (i > 0 && s.m[i] <= s.m[i - 1]) return SPCG_E_INVALID_ARG;
+  }
+  if (!(s.tol > 0.0) || s.max_iters < 0 || s.max_restarts < 0) return SPCG_E_INVALID_ARG;
+  return SPCG_OK;
+}
+
+spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
+  if (c->prof_used + 2 > c->prof_cap) {
+    // the stream is idle only after a sync; collect what is pending first
+    SPCG_CK(cudaStreamSynchronize(c->stream));
+    SPCG_TRY(prof_collect(c));
+    if (c->prof_cap == 0) {
+      c->prof_cap = 512;
+      c->prof_ev = (cudaEvent_t*)calloc(c->prof_cap, sizeof(cudaEvent_t));
+      if (!c->prof_ev) return SPCG_E_OOM;
+      for (int i = 0; i < c->prof_cap; ++i) SPCG_CK(cudaEventCreate(&c->prof_ev[i]));
+    }
+  }
+  *e0 = c->prof_ev[c->prof_used++];
+  *e1 = c->prof_ev[c->prof_used++];
+  return SPCG_OK;
+}
+
+spcg_status prof_collect(spcg_ctx* c) {
+  for (int i = 0; i + 1 < c->prof_used; i += 2) {
+    float ms = 0.f;
+    SPCG_CK(cudaEventElapsedTime(&ms, c->prof_ev[i], c->prof_ev[i + 1]));
+    c->prof_ms += ms;
+  }
+  c->prof_used = 0;
+  return SPCG_OK;
+}
+
+// Read the device scalars (synchronises the stream) and map the device
+// status to the ABI status.
+static spcg_status sync_scalars(spcg_ctx* c) {
+  SPCG_CK(cudaMemcpyAsync(&c->host_scal, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                          c->stream));
+  SPCG_CK(cudaStreamSynchronize(c->stream));
+  SPCG_TRY(prof_collect(c));
+  switch (c->host_scal.status) {
+    case DEV_OK: return SPCG_OK;
+    case DEV_BREAKDOWN: return SPCG_E_BREAKDOWN;
+    case DEV_TIMEOUT: return SPCG_E_TIMEOUT;
+    default: return SPCG_E_CUDA;
+  }
+}
+
+// g = A^T (b - A beta), u = R^{-T} g, z = R^{-1} u, dots: the PCG start.
+static spcg_status start_sequence(spcg_ctx* c, const PassGeom& g, const double* b,
+                                  double* beta, int& cur) {
+  SPCG_TRY(pass_resid(c, g, b, beta));
+  SPCG_TRY(launch_reduce(c, c->pb.g[cur], nullptr));
+  SPCG_TRY(launch_precond_T(c, 0, cur, 0, 0, beta));
+  cur ^= 1;
+  SPCG_TRY(launch_precond(c, cur, beta));
+  return SPCG_OK;
+}
+
+// One PCG iteration (four launches) after start_sequence or a previous one.
+static spcg_status iteration(spcg_ctx* c, const PassGeom& g, double* beta, int& cur, int& pp,
+                             int& gp, int start, int check, double tau) {
+  SPCG_TRY(pass_gram_iter(c, g, pp, gp, start, check, tau));
+  pp ^= 1;
+  gp ^= 1;
+  SPCG_TRY(launch_reduce(c, c->pb.w, c->pb.p[pp]));
+  SPCG_TRY(launch_precond_T(c, 1, cur, pp, gp, beta));
+  cur ^= 1;
+  SPCG_TRY(launch_precond(c, cur, beta));
+  return SPCG_OK;
+}
+
+static spcg_status run_stage(spcg_ctx* c, int i, int a_i, double* beta) {
+  const PassGeom& g = c->sk.geom[i];
+  SPCG_TRY(launch_reset_flags(c));
+  int cur = 0, pp = 0, gp = 0;
+  SPCG_TRY(start_sequence(c, g, c->sk.bK, beta, cur));
+  for (int k = 0; k < a_i; ++k) SPCG_TRY(iteration(c, g, beta, cur, pp, gp, k == 0, 0, 0.0));
+  return SPCG_OK;
+}
+
+struct RefineResult {
+  int iters = 0, restarts = 0, converged = 0;
+};
+
+static spcg_status run_refine(spcg_ctx* c, double tol, int max_iters, int max_restarts,
+                              double* beta, RefineResult* res) {
+  const double tau = tol / 2.0;
+  const PassGeom& g = c->gx;
+  int total = 0, restarts = 0;
+  SPCG_TRY(launch_reset_flags(c));
+  for (;;) {
+    // true gradient and the stopping test on it
+    int cur = 0, pp = 0, gp = 0;
+    SPCG_TRY(start_sequence(c, g, c->Y, beta, cur));
+    SPCG_TRY(launch_check(c, tau));
+    SPCG_TRY(sync_scalars(c));
+    if (c->host_scal.done) {
+      res->iters = total;
+      res->restarts = restarts;
+      res->converged = 1;
+      return SPCG_OK;
+    }
+    if (total >= max_iters || restarts > max_restarts) break;
+    int start = 1;
+    bool hit = false;
+    while (total < max_iters) {
+      const int remaining = max_iters - total;
+      const int chunk = remaining < 4 ? remaining : 4;
+      for (int k = 0; k < chunk; ++k) {
+        SPCG_TRY(iteration(c, g, beta, cur, pp, gp, start, 1, tau));
+        start = 0;
+      }
+      SPCG_TRY(sync_scalars(c));
+      total += c->host_scal.iters;
+      SPCG_TRY(launch_reset_flags(c));   // clears done and the iteration count
+      if (c->host_scal.done) {
+        hit = true;
+        break;
+      }
+    }
+    if (!hit) break;
+    ++restarts;
+  }
+  res->iters = total;
+  res->restarts = restarts;
+  res->converged = 0;
+  return SPCG_E_NOT_CONVERGED;
+}
+
+static void free_sketch(Sketch& s) {
+  dfree(s.gather);
+  dfree(s.dest);
+  dfree(s.hdest);
+  dfree(s.work);
+  dfree(s.AK);
+  dfree(s.bK);
+  dfree(s.Ahat);
+  s.ready = false;
+  s.mK_alloc = s.r_alloc = 0;
+  s.work_bytes = 0;
+  s.n_pad = 0;
+}
+
+}  // namespace spcg
+
+using namespace spcg;
+
+extern "C" const char* spcg_status_str(spcg_status s) {
+  switch (s) {
+    case SPCG_OK: return "SPCG_OK";
+    case SPCG_E_INVALID_ARG: return "SPCG_E_INVALID_ARG";
+    case SPCG_E_OOM: return "SPCG_E_OOM";
+    case SPCG_E_CUDA: return "SPCG_E_CUDA";
+    case SPCG_E_BREAKDOWN: return "SPCG_E_BREAKDOWN";
+    case SPCG_E_NOT_CONVERGED: return "SPCG_E_NOT_CONVERGED";
+    case SPCG_E_TIMEOUT: return "SPCG_E_TIMEOUT";
+    case SPCG_E_STATE: return "SPCG_E_STATE";
+  }
+  return "SPCG_E_UNKNOWN";
+}
+
+extern "C" spcg_status spcg_default_schedule(int64_t N, int32_t d, spcg_schedule* out) {
+  if (!out || d < 1 || N <= d) return SPCG_E_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  const int64_t n_pad = next_pow2(N);
+  int64_t m = next_pow2(8 * (int64_t)d);
+  int K = 0;
+  while (m <= n_pad / 2 && K < SPCG_MAX_STAGES) {
+    out->m[K] = m;
+    out->a[K] = 3;
+    ++K;
+    m *= 2;
+  }
+  out->K = K;
+  out->r = 6 * (int64_t)d < n_pad ? 6 * (int64_t)d : n_pad;
+  out->tol = 1e-6;
+  out->max_iters = 100;
+  out->max_restarts = 5;
+  return SPCG_OK;
+}
+
+extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, int32_t d,
+                                   int64_t ldx, void* stream, const spcg_opts* opts,
+                                   spcg_ctx** out) {
+  if (!out) return SPCG_E_INVALID_ARG;
+  *out = nullptr;
+  if (!X || !Y || d < 1 || d > SPCG_MAX_D || N <= d || N > (int64_t(1) << 30) || ldx < d)
+    return SPCG_E_INVALID_ARG;
+  spcg_ctx* c = new spcg_ctx();
+  c->stream = (cudaStream_t)stream;
+  if (opts) c->opts = *opts;
+  c->N = N;
+  c->d = d;
+  c->Y = Y;
+  spcg_status st = SPCG_OK;
+  auto fail = [&](spcg_status s) {
+    spcg_destroy(c);
+    return s;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(SPCG_E_CUDA);
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
+      cudaSuccess)
+    return fail(SPCG_E_CUDA);
+  // X: borrowed, or a padded copy when the row stride breaks the TMA rule
+  if ((ldx * 8) % 16 != 0 || ((uintptr_t)X & 15u) != 0) {
+    const int64_t ld2 = (d + 1) & ~int64_t(1);
+    if ((st = dalloc(&c->X_own, (size_t)N * ld2)) != SPCG_OK) return fail(st);
+    if (cudaMemcpy2DAsync(c->X_own, ld2 * 8, X, ldx * 8, (size_t)d * 8, N,
+                          cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      return fail(SPCG_E_CUDA);
+    c->X = c->X_own;
+    c->ldx = ld2;
+  } else {
+    c->X = X;
+    c->ldx = ldx;
+  }
+  if ((st = dalloc(&c->scal, 1)) != SPCG_OK) return fail(st);
+  if (cudaMemsetAsync(c->scal, 0, sizeof(DevScalars), c->stream) != cudaSuccess)
+    return fail(SPCG_E_CUDA);
+  PcgBuffers& pb = c->pb;
+  pb.grid = c->opts.grid_ctas > 0 ? c->opts.grid_ctas : c->num_sms;
+  int ni = 1;
+  while (ni * 32 < d) ni <<= 1;
+  pb.ldp = ni * 32;
+  pb.n_red = (d + 31) / 32;
+  pb.n_pre = (d + 3) / 4;
+  if ((st = dalloc(&pb.partials, (size_t)pb.grid * pb.ldp)) != SPCG_OK) return fail(st);
+  double** vecs[] = {&pb.w, &pb.u, &pb.z, &pb.g[0], &pb.g[1], &pb.p[0], &pb.p[1], &c->beta_work};
+  for (double** v : vecs) {
+    if ((st = dalloc(v, (size_t)d)) != SPCG_OK) return fail(st);
+    if (cudaMemsetAsync(*v, 0, (size_t)d * 8, c->stream) != cudaSuccess) return fail(SPCG_E_CUDA);
+  }
+  if ((st = dalloc(&pb.dots_pw, (size_t)pb.n_red)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&pb.dots_gz, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&pb.dots_rb, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
+  Sketch& s = c->sk;
+  if ((st = dalloc(&s.Rdiag, (size_t)d)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&s.R, (size_t)d * d)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&s.Rinv, (size_t)d * d)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&s.RinvT, (size_t)d * d)) != SPCG_OK) return fail(st);
+  if ((st = make_pass_geom(c->X, N, d, c->ldx, &c->gx)) != SPCG_OK) return fail(st);
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(SPCG_E_CUDA);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(SPCG_E_CUDA);
+  *out = c;
+  return SPCG_OK;
+}
+
+extern "C" void spcg_destroy(spcg_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_sketch(c->sk);
+  dfree(c->sk.Rdiag);
+  dfree(c->sk.R);
+  dfree(c->sk.Rinv);
+  dfree(c->sk.RinvT);
+  PcgBuffers& pb = c->pb;
+  dfree(pb.partials);
+  dfree(pb.w);
+  dfree(pb.u);
+  dfree(pb.z);
+  dfree(pb.g[0]);
+  dfree(pb.g[1]);
+  dfree(pb.p[0]);
+  dfree(pb.p[1]);
+  dfree(pb.dots_pw);
+  dfree(pb.dots_gz);
+  dfree(pb.dots_rb);
+  dfree(c->beta_work);
+  dfree(c->scal);
+  dfree(c->X_own);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (int i = 0; i < c->prof_cap; ++i)
+    if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
+  free(c->prof_ev);
+  delete c;
+}
+
+extern "C" spcg_status spcg_sketch(spcg_ctx* c, uint64_t seed, const spcg_schedule* sched) {
+  if (!c) return SPCG_E_INVALID_ARG;
+  spcg_schedule sc;
+  if (sched) sc = *sched;
+  else SPCG_TRY(spcg_default_schedule(c->N, c->d, &sc));
+  SPCG_TRY(validate_schedule(sc, c->N, c->d));
+  Sketch& s = c->sk;
+  s.ready = false;
+  const int d = c->d;
+  const int64_t n_pad = next_pow2(c->N);
+  const int nbits = ilog2(n_pad);
+  const int64_t mK = sc.K > 0 ? sc.m[sc.K - 1] : 0;
+  if (s.n_pad != n_pad) {
+    dfree(s.gather);
+    dfree(s.dest);
+    dfree(s.hdest);
+    SPCG_TRY(dalloc(&s.gather, (size_t)n_pad));
+    SPCG_TRY(dalloc(&s.dest, (size_t)n_pad));
+    SPCG_TRY(dalloc(&s.hdest, (size_t)n_pad));
+    s.n_pad = n_pad;
+  }
+  s.nbits = nbits;
+  const bool multipass = nbits > 12;
+  const size_t work_bytes = multipass ? (size_t)n_pad * (d + 1) * 8 : 0;
+  if (work_bytes > s.work_bytes) {
+    dfree(s.work);
+    SPCG_TRY(dalloc((unsigned char**)&s.work, work_bytes));
+    s.work_bytes = work_bytes;
+  }
+  s.ldw = d + 1;
+  s.ldak = (d + 1) & ~int64_t(1);
+  if (mK > s.mK_alloc) {
+    dfree(s.AK);
+    dfree(s.bK);
+    SPCG_TRY(dalloc(&s.AK, (size_t)mK * s.ldak));
+    SPCG_TRY(dalloc(&s.bK, (size_t)mK));
+    s.mK_alloc = mK;
+  }
+  if (sc.r > s.r_alloc) {
+    dfree(s.Ahat);
+    SPCG_TRY(dalloc(&s.Ahat, (size_t)sc.r * d));
+    s.r_alloc = sc.r;
+  }
+  s.seed = seed;
+  s.sched = sc;
+  if (s.ldak > d && mK > 0)   // padding columns of the prefix stay zero
+    SPCG_CK(cudaMemsetAsync(s.AK, 0, (size_t)mK * s.ldak * 8, c->stream));
+  for (int i = 0; i < sc.K; ++i) SPCG_TRY(make_pass_geom(s.AK, sc.m[i], d, s.ldak, &s.geom[i]));
+  SPCG_TRY(launch_reset_flags(c));
+  SPCG_TRY(launch_sketch_maps(c));
+  SPCG_TRY(launch_transform(c));
+  SPCG_TRY(launch_precond_factor(c));
+  SPCG_TRY(sync_scalars(c));
+  s.ready = true;
+  return SPCG_OK;
+}
+
+extern "C" spcg_status spcg_pcg_stage(spcg_ctx* c, int32_t i, int32_t a_i, double* beta) {
+  if (!c || !beta) return SPCG_E_INVALID_ARG;
+  if (!c->sk.ready) return SPCG_E_STATE;
+  if (i < 0 || i >= c->sk.sched.K || a_i < 0) return SPCG_E_INVALID_ARG;
+  SPCG_TRY(run_stage(c, i, a_i, beta));
+  return sync_scalars(c);
+}
+
+extern "C" spcg_status spcg_refine(spcg_ctx* c, double tol, int32_t max_iters, double* beta,
+                                   int32_t* iters_out) {
+  if (!c || !beta || !(tol > 0.0) || max_iters < 0) return SPCG_E_INVALID_ARG;
+  if (!c->sk.ready) return SPCG_E_STATE;
+  RefineResult rr;
+  spcg_status st = run_refine(c, tol, max_iters, c->sk.sched.max_restarts, beta, &rr);
+  if (iters_out) *iters_out = rr.iters;
+  return st;
+}
+
+extern "C" spcg_status spcg_solve(spcg_ctx* c, uint64_t seed, const spcg_schedule* sched,
+                                  double* beta, spcg_info* info) {
+  if (!c || !beta) return SPCG_E_INVALID_ARG;
+  if (info) memset(info, 0, sizeof(*info));
+  c->n_launch = c->n_pass = 0;
+  c->pass_bytes = 0;
+  c->prof_ms = 0.0;
+  SPCG_CK(cudaEventRecord(c->ev[0], c->stream));
+  SPCG_TRY(spcg_sketch(c, seed, sched));
+  SPCG_CK(cudaEventRecord(c->ev[1], c->stream));
+  const spcg_schedule& sc = c->sk.sched;
+  SPCG_CK(cudaMemsetAsync(c->beta_work, 0, (size_t)c->d * 8, c->stream));
+  for (int i = 0; i < sc.K; ++i) SPCG_TRY(run_stage(c, i, sc.a[i], c->beta_work));
+  SPCG_TRY(sync_scalars(c));
+  SPCG_CK(cudaEventRecord(c->ev[2], c->stream));
+  RefineResult rr;
+  spcg_status st = run_refine(c, sc.tol, sc.max_iters, sc.max_restarts, c->beta_work, &rr);
+  SPCG_CK(cudaEventRecord(c->ev[3], c->stream));
+  SPCG_CK(cudaMemcpyAsync(beta, c->beta_work, (size_t)c->d * 8, cudaMemcpyDeviceToDevice,
+                          c->stream));
+  SPCG_CK(cudaStreamSynchronize(c->stream));
+  SPCG_TRY(prof_collect(c));
+  if (info) {
+    info->K = sc.K;
+    info->pass_launches = (int32_t)c->n_pass;
+    info->launches = (int32_t)c->n_launch;
+    info->pass_ms = c->prof_ms;
+    for (int i = 0; i < sc.K; ++i) info->stage_iters[i] = sc.a[i];
+    info->refine_iters = rr.iters;
+    info->restarts = rr.restarts;
+    info->converged = rr.converged;
+    info->sqrt_gamma = c->host_scal.sqrt_gamma;
+    info->norm_R_beta = c->host_scal.norm_rb;
+    info->bytes_pass = c->pass_bytes;
+    float ms;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+    info->ms_sketch = ms;
+    cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
+    info->ms_stages = ms;
+    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+    info->ms_refine = ms;
+  }
+  return st;
+}
+
+extern "C" spcg_status spcg_export_sketch(spcg_ctx* c, int64_t row0, int64_t nrows, double* A,
+                                          double* b) {
+  if (!c || nrows < 0 || row0 < 0) return SPCG_E_INVALID_ARG;
+  if (!c->sk.ready) return SPCG_E_STATE;
+  const Sketch& s = c->sk;
+  const int64_t mK = s.sched.K > 0 ? s.sched.m[s.sched.K - 1] : 0;
+  if (row0 + nrows > mK) return SPCG_E_INVALID_ARG;
+  if (nrows == 0) return SPCG_OK;
+  if (A)
+    SPCG_CK(cudaMemcpy2DAsync(A, (size_t)c->d * 8, s.AK + row0 * s.ldak, (size_t)s.ldak * 8,
+                              (size_t)c->d * 8, nrows, cudaMemcpyDeviceToDevice, c->stream));
+  if (b)
+    SPCG_CK(cudaMemcpyAsync(b, s.bK + row0, (size_t)nrows * 8, cudaMemcpyDeviceToDevice,
+                            c->stream));
+  SPCG_CK(cudaStreamSynchronize(c->stream));
+  return SPCG_OK;
+}
+
+__global__ void k_colmajor_to_rowmajor(const double* __restrict__ src, int64_t r, int d,
+                                       double* __restrict__ dst) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < r * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / d, j = e % d;
+    dst[e] = src[j * r + i];
+  }
+}
+
+extern "C" spcg_status spcg_export_precond(spcg_ctx* c, double* R, double* Rinv, double* Ahat) {
+  if (!c) return SPCG_E_INVALID_ARG;
+  if (!c->sk.ready) return SPCG_E_STATE;
+  const size_t dd = (size_t)c->d * c->d * 8;
+  if (R) SPCG_CK(cudaMemcpyAsync(R, c->sk.R, dd, cudaMemcpyDeviceToDevice, c->stream));
+  if (Rinv) SPCG_CK(cudaMemcpyAsync(Rinv, c->sk.Rinv, dd, cudaMemcpyDeviceToDevice, c->stream));
+  if (Ahat) {
+    // Ahat is reduced in place by the QR; only R survives.  Re-run the
+    // transform into it when an export is asked for.
+    SPCG_TRY(launch_transform(c));
+    k_colmajor_to_rowmajor<<<256, 256, 0, c->stream>>>(c->sk.Ahat, c->sk.sched.r, c->d, Ahat);
+    SPCG_CK(cudaGetLastError());
+    // restore the factorised state expected by later calls
+    SPCG_TRY(launch_precond_factor(c));
+  }
+  return sync_scalars(c);
+}
+
+extern "C" spcg_status spcg_gram_apply(spcg_ctx* c, const double* A, int64_t m, int64_t lda,
+                                       const double* p, double* w) {
+  if (!c || !p || !w || m < 0) return SPCG_E_INVALID_ARG;
+  if (m == 0) {
+    SPCG_CK(cudaMemsetAsync(w, 0, (size_t)c->d * 8, c->stream));
+    SPCG_CK(cudaStreamSynchronize(c->stream));
+    return SPCG_OK;
+  }
+  if (!A) return SPCG_E_INVALID_ARG;
+  PassGeom g;
+  SPCG_TRY(make_pass_geom(A, m, c->d, lda, &g));
+  SPCG_TRY(launch_reset_flags(c));
+  SPCG_TRY(pass_gram_plain(c, g, p));
+  SPCG_TRY(launch_reduce(c, w, nullptr));
+  return sync_scalars(c);
+}

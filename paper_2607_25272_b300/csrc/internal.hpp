@@ -1,0 +1,146 @@
+// Host-side internals shared by the translation units of the SPCG library.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spcg.h"
+
+namespace spcg {
+
+// Device scalars of one context (one allocation, zeroed at create).
+struct DevScalars {
+  int status;        // DEV_* error code, sticky until the next spcg_* call
+  int done;          // stopping test passed (set by the pass prologue / check)
+  int iters;         // PCG iterations that ran a pass since the last reset
+  int pad;
+  double gam[2];     // gamma ping-pong
+  double sqrt_gamma; // last check: sqrt(gamma)
+  double norm_rb;    // last check: ||R beta||
+};
+
+// Geometry of the fused pass over one operand (rows of FP64 values).
+struct PassGeom {
+  int64_t m;     // rows
+  int d;         // columns
+  int nbox;      // TMA boxes across a row
+  int boxc;      // columns per box (even)
+  int tm;        // rows per tile (box height)
+  int ntiles;
+  int stages;
+  size_t stage_bytes;
+  size_t region_bytes;  // staging region (>= stages * stage_bytes and the reduction scratch)
+  size_t smem_bytes;
+  CUtensorMap tmap;
+};
+
+struct PcgBuffers {
+  double* partials;  // grid x ldp
+  int ldp;
+  int grid;          // CTAs of the fused pass
+  double* w;
+  double* u;
+  double* z;
+  double* g[2];
+  double* p[2];
+  double* dots_pw;   // per reduce CTA
+  double* dots_gz;   // per precond CTA
+  double* dots_rb;
+  int n_red;         // CTAs of the reduce kernel
+  int n_pre;         // CTAs of the precond kernels
+  int last_grid;     // CTAs of the last fused pass (= partials to reduce)
+};
+
+struct Sketch {
+  bool ready = false;
+  uint64_t seed = 0;
+  spcg_schedule sched{};
+  int64_t n_pad = 0;
+  int nbits = 0;
+  // random maps (N' entries)
+  uint32_t* gather = nullptr;   // P(j) | sign bit
+  int32_t* dest = nullptr;      // pi^{-1}(j) if < m_K else -1
+  int32_t* hdest = nullptr;     // sigma_hat^{-1}(j) if < r else -1
+  double* work = nullptr;       // N' x ldw transform buffer (multi-pass only)
+  int64_t ldw = 0;
+  size_t work_bytes = 0;
+  double* AK = nullptr;         // m_K x ldak sketched prefix (pi order)
+  int64_t ldak = 0;
+  double* bK = nullptr;         // m_K
+  int64_t mK_alloc = 0;
+  double* Ahat = nullptr;       // r x d column-major (ld = r), QR in place
+  int64_t r_alloc = 0;
+  double* Rdiag = nullptr;      // d
+  double* R = nullptr;          // d x d row-major upper
+  double* Rinv = nullptr;       // d x d row-major upper
+  double* RinvT = nullptr;      // d x d row-major lower (R^{-T})
+  PassGeom geom[SPCG_MAX_STAGES];  // fused-pass geometry of stage i (rows [0, m_i))
+};
+
+}  // namespace spcg
+
+struct spcg_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  spcg_opts opts{};
+  int64_t N = 0;
+  int d = 0;
+  const double* X = nullptr;   // caller's (or our padded copy)
+  int64_t ldx = 0;
+  double* X_own = nullptr;
+  const double* Y = nullptr;
+  spcg::DevScalars* scal = nullptr;
+  spcg::DevScalars host_scal{};
+  spcg::PcgBuffers pb{};
+  double* beta_work = nullptr;   // d
+  spcg::Sketch sk;
+  spcg::PassGeom gx{};           // pass geometry over X
+  bool gx_ready = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // launch accounting and optional per-pass event timing
+  int64_t n_launch = 0;
+  int64_t n_pass = 0;
+  uint64_t pass_bytes = 0;
+  cudaEvent_t* prof_ev = nullptr;   // pairs around fused-pass launches
+  int prof_cap = 0;
+  int prof_used = 0;
+  double prof_ms = 0.0;
+};
+
+namespace spcg {
+
+// Error helpers --------------------------------------------------------------
+spcg_status from_cuda(cudaError_t e);
+#define SPCG_CK(call)                                         \
+  do {                                                        \
+    cudaError_t e__ = (call);                                 \
+    if (e__ != cudaSuccess) return spcg::from_cuda(e__);      \
+  } while (0)
+#define SPCG_TRY(call)                                        \
+  do {                                                        \
+    spcg_status s__ = (call);                                 \
+    if (s__ != SPCG_OK) return s__;                           \
+  } while (0)
+
+// rng.cu
+spcg_status launch_sketch_maps(spcg_ctx* c);
+// fwht.cu
+spcg_status launch_transform(spcg_ctx* c);
+// qr.cu
+spcg_status launch_precond_factor(spcg_ctx* c);
+// pcg.cu
+spcg_status make_pass_geom(const double* A, int64_t m, int d, int64_t lda, PassGeom* g);
+spcg_status pass_resid(spcg_ctx* c, const PassGeom& g, const double* b, const double* x);
+spcg_status pass_gram_iter(spcg_ctx* c, const PassGeom& g, int pp, int gp, int start,
+                           int check, double tau);
+spcg_status launch_reduce(spcg_ctx* c, double* out, const double* dotvec);
+spcg_status launch_precond_T(spcg_ctx* c, int iter_mode, int cur, int pp, int gp, double* beta);
+spcg_status launch_precond(spcg_ctx* c, int cur, const double* beta);
+spcg_status launch_check(spcg_ctx* c, double tau);
+spcg_status launch_reset_flags(spcg_ctx* c);
+spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1);
+spcg_status prof_collect(spcg_ctx* c);   // after a stream sync
+spcg_status pass_gram_plain(spcg_ctx* c, const PassGeom& g, const double* p);
+
+}  // namespace spcg

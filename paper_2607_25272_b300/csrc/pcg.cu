@@ -1,0 +1,620 @@
+// PCG(A, b, H-hat, beta_init, a) of Sec. 2.2 on the normal equations,
+// preconditioned by H-hat = R^T R.  One iteration is
+//   w = A^T (A p); alpha = gamma / (p.w); beta += alpha p; g -= alpha w;
+//   z = R^{-1} (R^{-T} g); gamma' = g.z; p = z + (gamma'/gamma) p
+// (the d-space recurrence whose cost is the (4m + 13)d + 2d^2 flops that
+// Sec. 2.2 charges per iteration).  Kernels per iteration:
+//   k_pass      fused prologue (gamma', new p, stopping test) + one read of A:
+//               per-CTA partials of A^T (A p), row tiles staged by TMA
+//   k_reduce    partials -> w (fixed order) and partial dots p.w
+//   k_precondT  alpha, g update, beta update, u = R^{-T} g
+//   k_precond   z = R^{-1} u, partial dots g.z and ||R beta||^2
+// The stage start uses the same pass in residual mode: g = A^T (b - A beta).
+// All reductions run in a fixed order, so two runs give identical bits.
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace spcg {
+
+// --------------------------------------------------------------------------
+// mbarrier / TMA helpers (inline PTX, sm_90+ instructions used on sm_103a)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false once `budget` clock cycles have passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long budget) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr int kConsumers = 8;                 // consumer warps of k_pass
+constexpr int kPassThreads = 32 * (kConsumers + 1);
+constexpr int kMaxStages = 8;
+
+enum PassMode : int { PASS_PLAIN = 0, PASS_ITER = 1, PASS_RESID = 2 };
+
+struct PassArgs {
+  int64_t m;
+  int d, nbox, boxc, tm, ntiles, stages;
+  uint32_t tx_bytes;       // bytes one stage's boxes deliver
+  uint32_t slot_doubles;   // doubles between box slots (128-byte multiple)
+  uint32_t stage_doubles;  // doubles between stages
+  uint32_t region_doubles; // doubles of the staging region (also the reduction scratch)
+  int mode;
+  const double* vec;       // PLAIN: p; RESID: beta
+  const double* b;         // RESID: right-hand side
+  double* partials;
+  int ldp;
+  // PASS_ITER prologue
+  const double* z;
+  const double* p_prev;
+  double* p_next;
+  const double* dots_gz;
+  const double* dots_rb;
+  int n_dots;
+  int gp;                  // gamma ping-pong index of the previous direction
+  int start;               // 1: p = z (first iteration after a (re)start)
+  int check;               // 1: stop when sqrt(gamma) <= tau ||R beta||
+  double tau;
+  DevScalars* scal;
+  long long spin;
+  int inject_stall;        // test hook: CTA 0 never issues its first tile
+};
+
+// Fixed-order sum of n values by one warp: lanes stride, then xor tree.
+__device__ __forceinline__ double warp_sum_array(const double* v, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += v[i];
+  return warp_allsum(s);
+}
+
+template <int NI>
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant__ CUtensorMap tmap,
+                                                          const PassArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t base_addr = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((128u - (base_addr & 127u)) & 127u);
+  double* tiles = reinterpret_cast<double*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + (size_t)a.region_doubles);
+  uint64_t* empty = full + kMaxStages;
+  double* vec_s = reinterpret_cast<double*>(empty + kMaxStages);  // NI*32 doubles
+  __shared__ int s_flag;       // 1 = skip the pass (done / error)
+  __shared__ int s_abort;
+  __shared__ double s_scal[2];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (a.scal->status != 0 || a.scal->done != 0) return;   // uniform over the grid
+
+  if (tid == 0) {
+    s_flag = 0;
+    s_abort = 0;
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumers);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+
+  // ---- prologue: the direction this pass multiplies ----
+  if (a.mode == PASS_ITER) {
+    if (warp == 0) {
+      const double gam = warp_sum_array(a.dots_gz, a.n_dots);
+      const double rb2 = warp_sum_array(a.dots_rb, a.n_dots);
+      if (lane == 0) {
+        s_scal[0] = gam;
+        s_scal[1] = sqrt(rb2);
+      }
+    }
+    __syncthreads();
+    const double gam = s_scal[0], rb = s_scal[1];
+    int flag = 0;
+    if (!isfinite(gam) || gam < 0.0) flag = 2;
+    else if (gam == 0.0 || (a.check && sqrt(gam) <= a.tau * rb)) flag = 1;
+    if (flag) {
+      if (blockIdx.x == 0 && tid == 0) {
+        if (flag == 2) atomicExch(&a.scal->status, DEV_BREAKDOWN);
+        else {
+          a.scal->done = 1;
+          a.scal->sqrt_gamma = sqrt(gam);
+          a.scal->norm_rb = rb;
+        }
+      }
+      return;   // no TMA issued yet
+    }
+    const double ratio = a.start ? 0.0 : gam / a.scal->gam[a.gp];
+    for (int j = tid; j < NI * 32; j += blockDim.x) {
+      double v = 0.0;
+      if (j < a.d) v = a.z[j] + ratio * a.p_prev[j];
+      vec_s[j] = v;
+      if (blockIdx.x == 0 && j < a.d) a.p_next[j] = v;
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+      a.scal->gam[a.gp ^ 1] = gam;
+      a.scal->iters += 1;
+    }
+  } else {
+    for (int j = tid; j < NI * 32; j += blockDim.x) vec_s[j] = (j < a.d) ? a.vec[j] : 0.0;
+  }
+  __syncthreads();
+
+  const int my_tiles =
+      (blockIdx.x < a.ntiles) ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  double wacc[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) wacc[i] = 0.0;
+  int issued = 0, skipped = -1;   // producer thread (tid 0) only
+
+  if (warp == 0) {
+    // ---- producer: one lane issues the TMA box loads of each row tile ----
+    if (lane == 0) {
+      for (int k = 0; k < my_tiles; ++k) {
+        const int s = k % a.stages;
+        if (k >= a.stages) {
+          if (!mbar_wait_bounded(&empty[s], ((k / a.stages) - 1) & 1, a.spin)) {
+            atomicExch(&a.scal->status, DEV_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+        }
+        if (*(volatile int*)&s_abort) break;
+        issued = k + 1;
+        if (a.inject_stall && blockIdx.x == 0 && k == 0) {
+          skipped = 0;   // the consumers' wait on this tile can only time out
+          continue;
+        }
+        const int tile = blockIdx.x + k * gridDim.x;
+        mbar_expect_tx(&full[s], a.tx_bytes);
+        double* dst = tiles + (size_t)s * a.stage_doubles;
+        for (int bx = 0; bx < a.nbox; ++bx)
+          tma_load_2d(dst + (size_t)bx * a.slot_doubles, &tmap, bx * a.boxc, tile * a.tm,
+                      &full[s]);
+      }
+    }
+  } else {
+    // ---- consumers: t = a_row . v (warp all-reduce), acc += t a_row ----
+    const int cw = warp - 1;
+    int off[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int c = lane + 32 * i;
+      off[i] = (c < a.d) ? (c / a.boxc) * (int)a.slot_doubles + (c % a.boxc) : -1;
+    }
+    for (int k = 0; k < my_tiles; ++k) {
+      const int s = k % a.stages;
+      if (!mbar_wait_bounded(&full[s], (k / a.stages) & 1, a.spin)) {
+        atomicExch(&a.scal->status, DEV_TIMEOUT);
+        s_abort = 1;
+        break;
+      }
+      const int tile = blockIdx.x + k * gridDim.x;
+      const int64_t row0 = (int64_t)tile * a.tm;
+      const double* st = tiles + (size_t)s * a.stage_doubles;
+      for (int rr = cw; rr < a.tm; rr += kConsumers) {
+        if (row0 + rr >= a.m) break;
+        const double* rowp = st + rr * a.boxc;
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+          if (off[i] >= 0) t = fma(rowp[off[i]], vec_s[lane + 32 * i], t);
+        t = warp_allsum(t);
+        if (a.mode == PASS_RESID) t = a.b[row0 + rr] - t;
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+          if (off[i] >= 0) wacc[i] = fma(t, rowp[off[i]], wacc[i]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+  }
+  __syncthreads();
+
+  if (s_abort && tid == 0) {
+    // let every copy still in flight land before the CTA leaves (generous
+    // bound, independent of the caller's spin budget)
+    const int first = issued > a.stages ? issued - a.stages : 0;
+    for (int k = first; k < issued; ++k)
+      if (k != skipped)
+        (void)mbar_wait_bounded(&full[k % a.stages], (k / a.stages) & 1, 1ll << 31);
+  }
+  __syncthreads();
+
+  // ---- CTA partial: fixed-order sum over the consumer warps ----
+  double* red = tiles;   // reuse stage memory: kConsumers x (NI*32)
+  if (warp > 0) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) red[(warp - 1) * NI * 32 + lane + 32 * i] = wacc[i];
+  }
+  __syncthreads();
+  for (int j = tid; j < a.d; j += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kConsumers; ++w) s += red[w * NI * 32 + j];
+    a.partials[(size_t)blockIdx.x * a.ldp + j] = s;
+  }
+}
+
+// partials (nb x ldp) -> out[d]; optional per-CTA dots out.dotvec
+__global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ partials, int nb,
+                                                int ldp, int d, double* __restrict__ out,
+                                                const double* __restrict__ dotvec,
+                                                double* __restrict__ dots_out,
+                                                const DevScalars* __restrict__ scal) {
+  if (scal->status != 0 || scal->done != 0) return;
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (col < d)
+    for (int b = warp; b < nb; b += 8) s += partials[(size_t)b * ldp + col];
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    if (col < d) out[col] = t;
+    if (dotvec) {
+      double v = (col < d) ? t * dotvec[col] : 0.0;
+      v = warp_allsum(v);
+      if (lane == 0) dots_out[blockIdx.x] = v;
+    }
+  }
+}
+
+constexpr int kPreWarps = 4;
+
+// u = R^{-T} g_new (RinvT row-major lower); ITER mode first forms
+// alpha = gamma / p.w, g_new = g - alpha w and beta += alpha p.
+__global__ void __launch_bounds__(kPreWarps * 32)
+    k_precondT(int d, int iter_mode, const double* __restrict__ RinvT,
+               const double* __restrict__ g_cur, double* __restrict__ g_nxt,
+               const double* __restrict__ w, const double* __restrict__ p,
+               const double* __restrict__ dots_pw, int n_red, int gp, double* __restrict__ beta,
+               double* __restrict__ u, DevScalars* __restrict__ scal) {
+  if (scal->status != 0 || scal->done != 0) return;
+  extern __shared__ double gs[];
+  __shared__ double s_alpha;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double alpha = 0.0;
+  if (iter_mode) {
+    if (warp == 0) {
+      const double pw = warp_sum_array(dots_pw, n_red);
+      if (lane == 0) {
+        const double al = scal->gam[gp] / pw;
+        s_alpha = (pw > 0.0 && isfinite(al)) ? al : NAN;
+      }
+    }
+    __syncthreads();
+    alpha = s_alpha;
+    if (isnan(alpha)) {
+      if (threadIdx.x == 0) atomicExch(&scal->status, DEV_BREAKDOWN);
+      return;
+    }
+    for (int j = threadIdx.x; j < d; j += blockDim.x) gs[j] = fma(-alpha, w[j], g_cur[j]);
+  } else {
+    for (int j = threadIdx.x; j < d; j += blockDim.x) gs[j] = g_cur[j];
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kPreWarps + warp;
+  if (i >= d) return;
+  const double* Ri = RinvT + (size_t)i * d;
+  double s = 0.0;
+  for (int j = lane; j <= i; j += 32) s = fma(Ri[j], gs[j], s);
+  s = warp_allsum(s);
+  if (lane == 0) {
+    u[i] = s;
+    g_nxt[i] = gs[i];
+    if (iter_mode) beta[i] = fma(alpha, p[i], beta[i]);
+  }
+}
+
+// z = R^{-1} u; per-CTA partial dots g.z and ||R beta||^2.
+__global__ void __launch_bounds__(kPreWarps * 32)
+    k_precond(int d, const double* __restrict__ Rinv, const double* __restrict__ R,
+              const double* __restrict__ u, const double* __restrict__ beta,
+              const double* __restrict__ g, double* __restrict__ z,
+              double* __restrict__ dots_gz, double* __restrict__ dots_rb,
+              const DevScalars* __restrict__ scal) {
+  if (scal->status != 0 || scal->done != 0) return;
+  extern __shared__ double sh[];
+  double* us = sh;
+  double* bs = sh + d;
+  __shared__ double red[2][kPreWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    us[j] = u[j];
+    bs[j] = beta[j];
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kPreWarps + warp;
+  double gz = 0.0, rb2 = 0.0;
+  if (i < d) {
+    const double* Ri = Rinv + (size_t)i * d;
+    const double* Rr = R + (size_t)i * d;
+    double s = 0.0, q = 0.0;
+    for (int j = i + lane; j < d; j += 32) {
+      s = fma(Ri[j], us[j], s);
+      q = fma(Rr[j], bs[j], q);
+    }
+    s = warp_allsum(s);
+    q = warp_allsum(q);
+    if (lane == 0) z[i] = s;
+    gz = g[i] * s;
+    rb2 = q * q;
+  }
+  if (lane == 0) {
+    red[0][warp] = gz;
+    red[1][warp] = rb2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+#pragma unroll
+    for (int w = 0; w < kPreWarps; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    dots_gz[blockIdx.x] = a;
+    dots_rb[blockIdx.x] = b;
+  }
+}
+
+// The stopping test on freshly computed dots (same sums as the pass prologue).
+__global__ void k_check(const double* __restrict__ dots_gz, const double* __restrict__ dots_rb,
+                        int n, double tau, DevScalars* __restrict__ scal) {
+  if (scal->status != 0) return;
+  const double gam = warp_sum_array(dots_gz, n);
+  const double rb2 = warp_sum_array(dots_rb, n);
+  if (threadIdx.x == 0) {
+    const double rb = sqrt(rb2);
+    scal->sqrt_gamma = sqrt(fmax(gam, 0.0));
+    scal->norm_rb = rb;
+    if (!isfinite(gam) || gam < 0.0) scal->status = DEV_BREAKDOWN;
+    else scal->done = (gam == 0.0 || sqrt(gam) <= tau * rb) ? 1 : 0;
+  }
+}
+
+__global__ void k_reset(DevScalars* scal, int clear_status) {
+  if (clear_status) scal->status = 0;
+  scal->done = 0;
+  scal->iters = 0;
+}
+
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+static int ni_for(int d) {
+  const int n = (d + 31) / 32;
+  int ni = 1;
+  while (ni < n) ni <<= 1;
+  return ni;
+}
+
+spcg_status make_pass_geom(const double* A, int64_t m, int d, int64_t lda, PassGeom* g) {
+  if (m < 1 || d < 1 || d > SPCG_MAX_D || lda < d || (lda * 8) % 16 != 0 ||
+      ((uintptr_t)A & 15u) != 0)
+    return SPCG_E_INVALID_ARG;
+  g->m = m;
+  g->d = d;
+  g->nbox = (d + 255) / 256;
+  int bc = (d + g->nbox - 1) / g->nbox;
+  bc = (bc + 1) & ~1;   // box inner extent: a multiple of 16 bytes
+  g->boxc = bc;
+  const int row_bytes = g->nbox * bc * 8;
+  int tm = 32768 / row_bytes;
+  if (tm > 8) tm &= ~7;
+  if (tm < 1) tm = 1;
+  if (tm > 256) tm = 256;
+  if (tm > m) tm = (int)m;
+  g->tm = tm;
+  g->ntiles = (int)((m + tm - 1) / tm);
+  const size_t slot = (((size_t)tm * bc * 8) + 127) & ~(size_t)127;
+  const size_t stage = slot * g->nbox;
+  int stages = (int)((192 * 1024) / stage);
+  if (stages > kMaxStages) stages = kMaxStages;
+  if (stages < 2) stages = 2;
+  g->stages = stages;
+  g->stage_bytes = stage;
+  const size_t ni32 = (size_t)ni_for(d) * 32;
+  size_t red = (size_t)kConsumers * ni32 * 8;
+  size_t tiles = stage * stages;
+  if (tiles < red) tiles = red;
+  g->region_bytes = tiles;
+  g->smem_bytes = 128 + tiles + 2 * kMaxStages * 8 + ni32 * 8;
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return SPCG_E_CUDA;
+  cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)(lda * 8)};
+  cuuint32_t box[2] = {(cuuint32_t)bc, (cuuint32_t)tm};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(&g->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)A, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SPCG_OK : SPCG_E_CUDA;
+}
+
+template <int NI>
+static spcg_status launch_pass_ni(spcg_ctx* c, const PassGeom& g, const PassArgs& a, int grid) {
+  SPCG_CK(cudaFuncSetAttribute(k_pass<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)g.smem_bytes));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1));
+  if (e0) SPCG_CK(cudaEventRecord(e0, c->stream));
+  k_pass<NI><<<grid, kPassThreads, g.smem_bytes, c->stream>>>(g.tmap, a);
+  SPCG_CK(cudaGetLastError());
+  if (e1) SPCG_CK(cudaEventRecord(e1, c->stream));
+  c->n_launch += 1;
+  c->n_pass += 1;
+  c->pass_bytes += (uint64_t)g.m * g.d * 8;
+  return SPCG_OK;
+}
+
+static spcg_status launch_pass(spcg_ctx* c, const PassGeom& g, PassArgs a) {
+  int grid = c->pb.grid;
+  if (grid > g.ntiles) grid = g.ntiles;
+  if (grid < 1) grid = 1;
+  a.m = g.m;
+  a.d = g.d;
+  a.nbox = g.nbox;
+  a.boxc = g.boxc;
+  a.tm = g.tm;
+  a.ntiles = g.ntiles;
+  a.stages = g.stages;
+  a.tx_bytes = (uint32_t)((size_t)g.nbox * g.boxc * g.tm * 8);
+  a.slot_doubles = (uint32_t)(g.stage_bytes / g.nbox / 8);
+  a.stage_doubles = (uint32_t)(g.stage_bytes / 8);
+  a.region_doubles = (uint32_t)(g.region_bytes / 8);
+  a.partials = c->pb.partials;
+  a.ldp = c->pb.ldp;
+  a.scal = c->scal;
+  a.spin = c->opts.spin_budget > 0 ? c->opts.spin_budget : (1ll << 31);
+  a.inject_stall = c->opts.inject_stall;
+  c->pb.last_grid = grid;
+  switch (ni_for(g.d)) {
+    case 1: return launch_pass_ni<1>(c, g, a, grid);
+    case 2: return launch_pass_ni<2>(c, g, a, grid);
+    case 4: return launch_pass_ni<4>(c, g, a, grid);
+    case 8: return launch_pass_ni<8>(c, g, a, grid);
+    case 16: return launch_pass_ni<16>(c, g, a, grid);
+    case 32: return launch_pass_ni<32>(c, g, a, grid);
+    default: return SPCG_E_INVALID_ARG;
+  }
+}
+
+spcg_status pass_resid(spcg_ctx* c, const PassGeom& g, const double* b, const double* x) {
+  PassArgs a{};
+  a.mode = PASS_RESID;
+  a.vec = x;
+  a.b = b;
+  return launch_pass(c, g, a);
+}
+
+spcg_status pass_gram_plain(spcg_ctx* c, const PassGeom& g, const double* p) {
+  PassArgs a{};
+  a.mode = PASS_PLAIN;
+  a.vec = p;
+  return launch_pass(c, g, a);
+}
+
+spcg_status pass_gram_iter(spcg_ctx* c, const PassGeom& g, int pp, int gp, int start, int check,
+                           double tau) {
+  PassArgs a{};
+  a.mode = PASS_ITER;
+  a.z = c->pb.z;
+  a.p_prev = c->pb.p[pp];
+  a.p_next = c->pb.p[pp ^ 1];
+  a.dots_gz = c->pb.dots_gz;
+  a.dots_rb = c->pb.dots_rb;
+  a.n_dots = c->pb.n_pre;
+  a.gp = gp;
+  a.start = start;
+  a.check = check;
+  a.tau = tau;
+  return launch_pass(c, g, a);
+}
+
+spcg_status launch_reduce(spcg_ctx* c, double* out, const double* dotvec) {
+  const int d = c->d;
+  const int nr = (d + 31) / 32;
+  k_reduce<<<nr, 256, 0, c->stream>>>(c->pb.partials, c->pb.last_grid, c->pb.ldp, d, out, dotvec,
+                                      c->pb.dots_pw, c->scal);
+  SPCG_CK(cudaGetLastError());
+  c->n_launch += 1;
+  return SPCG_OK;
+}
+
+spcg_status launch_precond_T(spcg_ctx* c, int iter_mode, int cur, int pp, int gp, double* beta) {
+  const int d = c->d;
+  const int nb = (d + kPreWarps - 1) / kPreWarps;
+  k_precondT<<<nb, kPreWarps * 32, (size_t)d * 8, c->stream>>>(
+      d, iter_mode, c->sk.RinvT, c->pb.g[cur], c->pb.g[cur ^ 1], c->pb.w, c->pb.p[pp],
+      c->pb.dots_pw, (d + 31) / 32, gp, beta, c->pb.u, c->scal);
+  SPCG_CK(cudaGetLastError());
+  c->n_launch += 1;
+  return SPCG_OK;
+}
+
+spcg_status launch_precond(spcg_ctx* c, int cur, const double* beta) {
+  const int d = c->d;
+  const int nb = (d + kPreWarps - 1) / kPreWarps;
+  k_precond<<<nb, kPreWarps * 32, (size_t)2 * d * 8, c->stream>>>(
+      d, c->sk.Rinv, c->sk.R, c->pb.u, beta, c->pb.g[cur], c->pb.z, c->pb.dots_gz,
+      c->pb.dots_rb, c->scal);
+  SPCG_CK(cudaGetLastError());
+  c->n_launch += 1;
+  return SPCG_OK;
+}
+
+spcg_status launch_check(spcg_ctx* c, double tau) {
+  k_check<<<1, 32, 0, c->stream>>>(c->pb.dots_gz, c->pb.dots_rb, c->pb.n_pre, tau, c->scal);
+  SPCG_CK(cudaGetLastError());
+  c->n_launch += 1;
+  return SPCG_OK;
+}
+
+spcg_status launch_reset_flags(spcg_ctx* c) {
+  k_reset<<<1, 1, 0, c->stream>>>(c->scal, 1);
+  SPCG_CK(cudaGetLastError());
+  c->n_launch += 1;
+  return SPCG_OK;
+}
+
+}  // namespace spcg

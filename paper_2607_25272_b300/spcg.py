@@ -1,0 +1,309 @@
+"""Python binding of the SPCG C ABI (include/spcg.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA library ``libspcg.so`` that sits
+next to this file; this module converts torch CUDA tensors (device memory
+and streams) and Python values to the C calls and back.  There is no CPU
+fallback: if the library is missing or fails to load, every call raises.
+
+The functions keep the C names (``spcg_create``, ``spcg_sketch``,
+``spcg_pcg_stage``, ``spcg_refine``, ``spcg_solve``, ...); ``Solver`` is a
+thin owner of one context.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspcg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "spcg.h")
+
+MAX_STAGES = 40
+MAX_D = 1024
+
+STATUS = {
+    0: "SPCG_OK",
+    1: "SPCG_E_INVALID_ARG",
+    2: "SPCG_E_OOM",
+    3: "SPCG_E_CUDA",
+    4: "SPCG_E_BREAKDOWN",
+    5: "SPCG_E_NOT_CONVERGED",
+    6: "SPCG_E_TIMEOUT",
+    7: "SPCG_E_STATE",
+}
+SPCG_OK = 0
+SPCG_E_INVALID_ARG = 1
+SPCG_E_OOM = 2
+SPCG_E_CUDA = 3
+SPCG_E_BREAKDOWN = 4
+SPCG_E_NOT_CONVERGED = 5
+SPCG_E_TIMEOUT = 6
+SPCG_E_STATE = 7
+
+PREC_FP64 = 0
+
+
+class SpcgError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int32),
+        ("m", ctypes.c_int64 * MAX_STAGES),
+        ("a", ctypes.c_int32 * MAX_STAGES),
+        ("r", ctypes.c_int64),
+        ("tol", ctypes.c_double),
+        ("max_iters", ctypes.c_int32),
+        ("max_restarts", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {"m": list(self.m[: self.K]), "a": list(self.a[: self.K]), "r": self.r,
+                "tol": self.tol, "max_iters": self.max_iters, "max_restarts": self.max_restarts}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("grid_ctas", ctypes.c_int32),
+        ("spin_budget", ctypes.c_int64),
+        ("inject_stall", ctypes.c_int32),
+        ("profile", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int32),
+        ("stage_iters", ctypes.c_int32 * MAX_STAGES),
+        ("refine_iters", ctypes.c_int32),
+        ("restarts", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("sqrt_gamma", ctypes.c_double),
+        ("norm_R_beta", ctypes.c_double),
+        ("ms_sketch", ctypes.c_double),
+        ("ms_stages", ctypes.c_double),
+        ("ms_refine", ctypes.c_double),
+        ("bytes_pass", ctypes.c_uint64),
+        ("pass_launches", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
+        ("pass_ms", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "spcg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "spcg_default_schedule": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Schedule)]),
+    "spcg_create": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P,
+                                   ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "spcg_destroy": (None, [_P]),
+    "spcg_sketch": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Schedule)]),
+    "spcg_pcg_stage": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "spcg_refine": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32, _P,
+                                   ctypes.POINTER(ctypes.c_int32)]),
+    "spcg_solve": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Schedule), _P,
+                                  ctypes.POINTER(Info)]),
+    "spcg_philox": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, _P, _P]),
+    "spcg_feistel": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                    ctypes.c_int32, _P, _P]),
+    "spcg_signs": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, _P, _P]),
+    "spcg_export_sketch": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "spcg_export_precond": (ctypes.c_int, [_P, _P, _P, _P]),
+    "spcg_gram_apply": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+}
+
+
+def declared_symbols():
+    """Names of the functions include/spcg.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spcg_[a-z_0-9]+)\s*\(", text)))
+
+
+def lib():
+    """Load libspcg.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"SPCG CUDA library not built: {LIB_PATH} is missing "
+                               "(run python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st, where):
+    if st != SPCG_OK:
+        raise SpcgError(st, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def status_str(st):
+    return lib().spcg_status_str(st).decode()
+
+
+def spcg_default_schedule(N, d):
+    s = Schedule()
+    _check(lib().spcg_default_schedule(N, d, ctypes.byref(s)), "spcg_default_schedule")
+    return s
+
+
+def make_schedule(m, a, r, tol=1e-6, max_iters=100, max_restarts=5):
+    s = Schedule()
+    s.K = len(m)
+    for i, (mi, ai) in enumerate(zip(m, a)):
+        s.m[i] = int(mi)
+        s.a[i] = int(ai)
+    s.r = int(r)
+    s.tol = float(tol)
+    s.max_iters = int(max_iters)
+    s.max_restarts = int(max_restarts)
+    return s
+
+
+def spcg_philox(ctr, seed, out=None, stream=None):
+    """ctr: CUDA uint32 tensor of shape (n, 4) (or int32 view); returns (n, 4)."""
+    import torch
+    n = ctr.shape[0]
+    if out is None:
+        out = torch.empty_like(ctr)
+    _check(lib().spcg_philox(_ptr(ctr), seed, n, _ptr(out), _stream_ptr(stream)), "spcg_philox")
+    return out
+
+
+def spcg_feistel(seed, nbits, tag, count, inverse=False, stream=None):
+    import torch
+    out = torch.empty(max(count, 1), dtype=torch.int64, device="cuda")
+    _check(lib().spcg_feistel(seed, nbits, tag, count, int(inverse), _ptr(out), _stream_ptr(stream)),
+           "spcg_feistel")
+    return out[:count]
+
+
+def spcg_signs(seed, n, stream=None):
+    import torch
+    out = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    _check(lib().spcg_signs(seed, n, _ptr(out), _stream_ptr(stream)), "spcg_signs")
+    return out[:n]
+
+
+class Solver:
+    """Owner of one spcg_ctx over device-resident (X, Y)."""
+
+    def __init__(self, X, Y, opts=None, stream=None):
+        import torch
+        if X.dtype != torch.float64 or Y.dtype != torch.float64:
+            raise ValueError("X and Y must be float64")
+        if X.dim() != 2 or X.stride(1) != 1:
+            raise ValueError("X must be a row-major 2-D tensor")
+        self.N, self.d = X.shape
+        self.X, self.Y = X, Y   # keep the borrowed buffers alive
+        self.stream = stream
+        ctx = ctypes.c_void_p()
+        o = ctypes.byref(opts) if opts is not None else None
+        _check(lib().spcg_create(_ptr(X), _ptr(Y), self.N, self.d, X.stride(0),
+                                 _stream_ptr(stream), o, ctypes.byref(ctx)), "spcg_create")
+        self.ctx = ctx
+
+    def close(self):
+        if self.ctx:
+            lib().spcg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sketch(self, seed, sched=None):
+        _check(lib().spcg_sketch(self.ctx, seed, ctypes.byref(sched) if sched else None),
+               "spcg_sketch")
+
+    def pcg_stage(self, i, a_i, beta):
+        _check(lib().spcg_pcg_stage(self.ctx, i, a_i, _ptr(beta)), "spcg_pcg_stage")
+        return beta
+
+    def refine(self, tol, max_iters, beta, raise_on_error=True):
+        it = ctypes.c_int32(0)
+        st = lib().spcg_refine(self.ctx, tol, max_iters, _ptr(beta), ctypes.byref(it))
+        if raise_on_error:
+            _check(st, "spcg_refine")
+        return st, it.value
+
+    def solve(self, seed, sched=None, beta=None, raise_on_error=True):
+        import torch
+        if beta is None:
+            beta = torch.empty(self.d, dtype=torch.float64, device=self.X.device)
+        info = Info()
+        st = lib().spcg_solve(self.ctx, seed, ctypes.byref(sched) if sched else None,
+                              _ptr(beta), ctypes.byref(info))
+        if raise_on_error:
+            _check(st, "spcg_solve")
+        return beta, info, st
+
+    def export_sketch(self, row0, nrows):
+        import torch
+        A = torch.empty((max(nrows, 1), self.d), dtype=torch.float64, device=self.X.device)
+        b = torch.empty(max(nrows, 1), dtype=torch.float64, device=self.X.device)
+        _check(lib().spcg_export_sketch(self.ctx, row0, nrows, _ptr(A), _ptr(b)),
+               "spcg_export_sketch")
+        return A[:nrows], b[:nrows]
+
+    def export_precond(self, r=None):
+        import torch
+        d = self.d
+        R = torch.empty((d, d), dtype=torch.float64, device=self.X.device)
+        Rinv = torch.empty((d, d), dtype=torch.float64, device=self.X.device)
+        Ahat = None
+        if r is not None:
+            Ahat = torch.empty((r, d), dtype=torch.float64, device=self.X.device)
+        _check(lib().spcg_export_precond(self.ctx, _ptr(R), _ptr(Rinv), _ptr(Ahat)),
+               "spcg_export_precond")
+        return R, Rinv, Ahat
+
+    def gram_apply(self, A, p, w=None):
+        import torch
+        if w is None:
+            w = torch.empty(self.d, dtype=torch.float64, device=p.device)
+        m = A.shape[0]
+        lda = A.stride(0) if m > 0 else self.d
+        st = lib().spcg_gram_apply(self.ctx, _ptr(A) if m > 0 else None, m, lda, _ptr(p), _ptr(w))
+        _check(st, "spcg_gram_apply")
+        return w
+
+
+def spcg_solve_host(X_host, Y_host, seed, sched=None, opts=None):
+    """End-to-end call from pinned host buffers: H2D copy, solve, D2H of beta."""
+    import torch
+    X = X_host.to("cuda", non_blocking=True)
+    Y = Y_host.to("cuda", non_blocking=True)
+    s = Solver(X, Y, opts)
+    try:
+        beta, info, st = s.solve(seed, sched)
+        return beta.cpu(), info, st
+    finally:
+        s.close()

@@ -1,0 +1,63 @@
+"""Host-side checks of the C ABI: the library loads, exports every function
+include/spcg.h declares, and its host-only entry points (no CUDA call)
+agree with the oracle's schedule reading of Sec. 4."""
+import ctypes
+
+import pytest
+
+from oracle.spcg import default_schedule
+from paper_2607_25272_b300 import spcg as S
+
+
+def test_library_exports_every_declared_symbol():
+    L = S.lib()
+    names = S.declared_symbols()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(S._SIGS)
+
+
+def test_status_strings():
+    for code, name in S.STATUS.items():
+        assert S.status_str(code) == name
+    assert S.status_str(99) == "SPCG_E_UNKNOWN"
+
+
+@pytest.mark.parametrize("N,d", [(20000, 50), (1 << 20, 500), (1 << 22, 1000), (1 << 23, 256),
+                                 (3000, 37), (100, 50), (5000, 1), (1 << 17, 64)])
+def test_default_schedule_matches_oracle_reading(N, d):
+    s = S.spcg_default_schedule(N, d)
+    o = default_schedule(N, d)
+    assert list(s.m[: s.K]) == o["m"]
+    assert list(s.a[: s.K]) == o["a"]
+    assert s.r == min(o["r"], o["n_pad"])
+    assert s.tol == 1e-6 and s.max_iters == 100
+
+
+def test_invalid_arguments_rejected_before_any_cuda_call():
+    L = S.lib()
+    out = ctypes.c_void_p()
+    # null X / Y, d out of range, N <= d: SPCG_E_INVALID_ARG, ctx stays NULL
+    assert L.spcg_create(None, None, 100, 5, 5, None, None, ctypes.byref(out)) == S.SPCG_E_INVALID_ARG
+    assert out.value is None
+    fake = ctypes.c_void_p(16)
+    assert L.spcg_create(fake, fake, 100, 0, 5, None, None, ctypes.byref(out)) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_create(fake, fake, 5, 5, 5, None, None, ctypes.byref(out)) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_create(fake, fake, 100, 2000, 2000, None, None, ctypes.byref(out)) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_create(fake, fake, 100, 5, 4, None, None, ctypes.byref(out)) == S.SPCG_E_INVALID_ARG
+    sch = S.Schedule()
+    assert L.spcg_default_schedule(10, 10, ctypes.byref(sch)) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_default_schedule(10, 3, None) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_sketch(None, 1, None) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_pcg_stage(None, 0, 1, None) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_solve(None, 1, None, None, None) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_feistel(1, 31, 0, 1, 0, None, None) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_feistel(1, 4, 0, 17, 0, fake, None) == S.SPCG_E_INVALID_ARG
+    L.spcg_destroy(None)   # no-op
+
+
+def test_struct_layouts_match_header_sizes():
+    # spcg_schedule: int32 K, int64 m[40], int32 a[40], int64 r, double tol, 2 x int32
+    assert ctypes.sizeof(S.Schedule) == 8 + 8 * 40 + 4 * 40 + 8 + 8 + 8
+    assert ctypes.sizeof(S.Opts) == 4 + 4 + 8 + 16
