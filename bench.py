@@ -36,6 +36,8 @@ WORKLOADS = {
                N=20000, d=50, kappa=None, sigma=1.0, seed=1, tol=1e-6),
 }
 CPU_SAMPLE_ROWS = 1 << 17     # oracle row sample for the CPU baseline
+# ncu: k_pass (FP64) on 262144 x 500 read 1.048667 GB + wrote 3.14 MB for 1.048576 GB of rows
+K_PASS_TRAFFIC_RATIO = (1.048667e9 + 3.142912e6) / 1.048576e9
 
 
 def make_problem(w, N=None, seed_offset=0):
@@ -282,7 +284,10 @@ def run_ours(args, w, rank, world, local_rank):
                 "frac": ach_tflops / fp64_peak_tflops,
                 "peak_source": "nominal B300 FP64 1.25 TFLOP/s (recipe table); FP64 FMA probe "
                                "measured 1.13 TFLOP/s",
-                "traffic": None,
+                # DRAM read+write bytes per launch from the ncu capture of this kernel on a
+                # 262144 x 500 operand (profiles/k_pass_fp64_gram_262144x500.md), scaled by
+                # rows to the average launch of the solve; None once the kernel changes.
+                "traffic": bytes_per_launch * K_PASS_TRAFFIC_RATIO if K_PASS_TRAFFIC_RATIO else None,
                 "hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm_gbs / hbm_peak,
                 "hbm_peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
                 "pass_launches_per_step": pass_n / args.steps,
