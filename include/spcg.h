@@ -240,6 +240,31 @@ spcg_status spcg_export_precond(spcg_ctx* ctx, double* R, double* Rinv, double* 
 spcg_status spcg_gram_apply(spcg_ctx* ctx, const double* A, int64_t m, int64_t lda,
                             const double* p, double* w);
 
+/*
+ * Allocation-free form of spcg_gram_apply: w = A^T (A p) in one read of A,
+ * with no context and no device allocation of any kind.  (The paper has no
+ * counterpart; this entry point serves callers that cannot allocate device
+ * memory, e.g. code running under a caching allocator that owns the device
+ * pool, in a memory-capped sandbox, or where an allocation would force a
+ * device-wide synchronisation.)
+ *   A       device, m x d row-major FP64, lda >= d, lda*8 % 16 == 0, A 16-byte
+ *           aligned (the TMA rules); m >= 0 (m = 0 gives w = 0)
+ *   p, w    device, d FP64
+ *   d       1 <= d <= SPCG_MAX_D (1024): the scratch holds partial sums for at
+ *           most 1024 columns; larger d returns SPCG_E_INVALID_ARG
+ *   stream  cudaStream_t; the call synchronises it before returning
+ * Scratch: a fixed 1,310,976-byte __device__ array inside the library (per-CTA
+ * partial sums for up to 160 CTAs x 1024 columns plus a status word), held by
+ * every GPU that loads the library until the process exits.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current, so make the first call on each device outside any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race and
+ * may return wrong results.
+ * Errors: SPCG_E_INVALID_ARG, SPCG_E_CUDA, SPCG_E_TIMEOUT.
+ */
+spcg_status spcg_gram_apply_noalloc(const double* A, int64_t m, int32_t d, int64_t lda,
+                                    const double* p, double* w, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

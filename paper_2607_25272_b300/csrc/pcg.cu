@@ -618,3 +618,57 @@ spcg_status launch_reset_flags(spcg_ctx* c) {
 }
 
 }  // namespace spcg
+
+namespace spcg {
+
+// The fused pass (plain mode) and the partial-sum reduction with scratch
+// that the caller provides: `partials` holds grid x ldp doubles and `scal`
+// one DevScalars whose status and done words the caller has cleared.
+template <int NI>
+static spcg_status launch_gram_scratch_ni(const PassGeom& g, const PassArgs& a, int grid,
+                                          cudaStream_t st) {
+  SPCG_CK(cudaFuncSetAttribute(k_pass<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)g.smem_bytes));
+  k_pass<NI><<<grid, kPassThreads, g.smem_bytes, st>>>(g.tmap, a);
+  SPCG_CK(cudaGetLastError());
+  return SPCG_OK;
+}
+
+spcg_status launch_gram_with_scratch(const PassGeom& g, const double* p, double* w,
+                                     double* partials, int ldp, int grid, DevScalars* scal,
+                                     cudaStream_t st) {
+  PassArgs a{};
+  a.mode = PASS_PLAIN;
+  a.vec = p;
+  a.m = g.m;
+  a.d = g.d;
+  a.nbox = g.nbox;
+  a.boxc = g.boxc;
+  a.tm = g.tm;
+  a.ntiles = g.ntiles;
+  a.stages = g.stages;
+  a.tx_bytes = (uint32_t)((size_t)g.nbox * g.boxc * g.tm * 8);
+  a.slot_doubles = (uint32_t)(g.stage_bytes / g.nbox / 8);
+  a.stage_doubles = (uint32_t)(g.stage_bytes / 8);
+  a.region_doubles = (uint32_t)(g.region_bytes / 8);
+  a.partials = partials;
+  a.ldp = ldp;
+  a.scal = scal;
+  a.spin = 1ll << 31;
+  spcg_status s;
+  switch (ni_for(g.d)) {
+    case 1: s = launch_gram_scratch_ni<1>(g, a, grid, st); break;
+    case 2: s = launch_gram_scratch_ni<2>(g, a, grid, st); break;
+    case 4: s = launch_gram_scratch_ni<4>(g, a, grid, st); break;
+    case 8: s = launch_gram_scratch_ni<8>(g, a, grid, st); break;
+    case 16: s = launch_gram_scratch_ni<16>(g, a, grid, st); break;
+    case 32: s = launch_gram_scratch_ni<32>(g, a, grid, st); break;
+    default: return SPCG_E_INVALID_ARG;
+  }
+  if (s != SPCG_OK) return s;
+  k_reduce<<<(g.d + 31) / 32, 256, 0, st>>>(partials, grid, ldp, g.d, w, nullptr, nullptr, scal);
+  SPCG_CK(cudaGetLastError());
+  return SPCG_OK;
+}
+
+}  // namespace spcg

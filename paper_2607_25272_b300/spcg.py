@@ -116,6 +116,8 @@ _SIGS = {
     "spcg_export_sketch": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
     "spcg_export_precond": (ctypes.c_int, [_P, _P, _P, _P]),
     "spcg_gram_apply": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "spcg_gram_apply_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                               _P, _P, _P]),
 }
 
 
@@ -294,6 +296,24 @@ class Solver:
         st = lib().spcg_gram_apply(self.ctx, _ptr(A) if m > 0 else None, m, lda, _ptr(p), _ptr(w))
         _check(st, "spcg_gram_apply")
         return w
+
+
+def spcg_gram_apply_noalloc(A, p, w=None, stream=None):
+    """w = A^T (A p) through the allocation-free entry point.
+
+    For callers that may not allocate device memory: the library uses its own
+    fixed device scratch array (shared by all calls; calls that overlap on the
+    GPU race).  The output w may be supplied so that nothing is allocated here
+    either."""
+    import torch
+    m, d = A.shape
+    if w is None:
+        w = torch.empty(d, dtype=torch.float64, device=p.device)
+    lda = A.stride(0) if m > 0 else d
+    st = lib().spcg_gram_apply_noalloc(_ptr(A) if m > 0 else None, m, d, lda, _ptr(p), _ptr(w),
+                                       _stream_ptr(stream))
+    _check(st, "spcg_gram_apply_noalloc")
+    return w
 
 
 def spcg_solve_host(X_host, Y_host, seed, sched=None, opts=None):
