@@ -174,3 +174,22 @@ def spcg(X, Y, seed, schedule=None, tol=1e-6, beta0=None, max_iters=100,
     return {"beta": beta, "R": R, "A_hat": A_hat, "stage_betas": stage_betas,
             "stage_iters": list(schedule["a"]), "refine_iters": s_iters,
             "converged": converged, "schedule": schedule}
+
+
+def tuned_schedule(N, d, a=4):
+    """The tuned sketch-size schedule of Sec. 4.3, generalised in d and N.
+
+    For N = 2^22, d = 2^6 the paper uses m_i in {2^10, ..., 2^16} followed by a
+    single subproblem of size 2^20 and a_i = 4.  Reading: m_1 = 2^ceil(log2 16d)
+    (= 2^10 at d = 64), seven doublings at most, all below N'/4, then one
+    transition stage of size N'/4 (= 2^20 at N = 2^22); r = 6d.
+    """
+    n_pad = 1 << (int(N) - 1).bit_length()
+    m = []
+    mi = 1 << (16 * d - 1).bit_length()
+    while len(m) < 7 and mi < n_pad // 4:
+        m.append(mi)
+        mi *= 2
+    if n_pad // 4 > (m[-1] if m else 0) and n_pad // 4 > 6 * d:
+        m.append(n_pad // 4)
+    return {"m": m, "a": [a] * len(m), "r": 6 * d, "n_pad": n_pad}
