@@ -54,7 +54,14 @@ typedef enum {
 
 /* Arithmetic of the X^T(Xp) passes (spcg_opts.precision). */
 enum {
-  SPCG_PREC_FP64 = 0        /* plain FP64 everywhere (the comparator path)    */
+  SPCG_PREC_FP64 = 0,       /* plain FP64 everywhere (the comparator path)    */
+  SPCG_PREC_MIXED = 1       /* Stage I reads a BF16 copy of the sketched rows
+                               with FP32 accumulation; Stage II iterates on an
+                               FP32 copy of X with compensated (TwoProd/TwoSum)
+                               accumulation, and every true gradient
+                               X^T (Y - X beta) that the stopping rule trusts is
+                               an FP64 pass over X; the sketch, the QR giving R,
+                               R^{-1} and the CG scalars stay FP64            */
 };
 
 /*
@@ -82,7 +89,17 @@ typedef struct {
   double tol;
   int32_t max_iters;
   int32_t max_restarts;
+  int32_t sketch;           /* SPCG_SKETCH_SRHT or SPCG_SKETCH_COUNT          */
 } spcg_schedule;
+
+/* Sketching operator of the initialisation (spcg_schedule.sketch). */
+enum {
+  SPCG_SKETCH_SRHT = 0,     /* nested SRHT (Sec. 2.1, Sec. 2.2)               */
+  SPCG_SKETCH_COUNT = 1     /* CountSketch, SPCG-CS (Sec. 4.3): one hash into
+                               m_K buckets folded modulo m_i for stage i (all
+                               m_i powers of two), an independent r-bucket
+                               CountSketch for the preconditioner              */
+};
 
 typedef struct {
   int32_t precision;        /* SPCG_PREC_*                                     */
@@ -125,6 +142,15 @@ const char* spcg_status_str(spcg_status s);
  * Errors: SPCG_E_INVALID_ARG for out == NULL, d < 1, N <= d.
  */
 spcg_status spcg_default_schedule(int64_t N, int32_t d, spcg_schedule* out);
+
+/*
+ * The tuned schedule of Sec. 4.3: for N = 2^22, d = 2^6 the paper uses
+ * m_i = 2^10, ..., 2^16 followed by a single 2^20 subproblem and a_i = 4.
+ * Generalised: m_1 = 2^ceil(log2 16d), at most seven doublings below N'/4,
+ * then one transition stage of N'/4 rows; r = 6d; tol, limits as the default.
+ * Host-only.  Errors: SPCG_E_INVALID_ARG as spcg_default_schedule.
+ */
+spcg_status spcg_tuned_schedule(int64_t N, int32_t d, spcg_schedule* out);
 
 /*
  * Create a solver context for the problem (X, Y) of Eq. (model).
@@ -215,11 +241,13 @@ spcg_status spcg_feistel(uint64_t seed, int32_t nbits, int32_t tag, int64_t coun
 spcg_status spcg_signs(uint64_t seed, int64_t n, double* out, void* stream);
 
 /*
- * Copy rows [row0, row0 + nrows) of the sketched prefix after spcg_sketch:
- *   A  device, nrows x d row-major (leading dimension d): Z[pi(t), :]
- *   b  device, nrows (may be NULL): Z_Y[pi(t)]
- * (Z normalised by 1/sqrt(N'); stage i's pair is sqrt(N'/m_i) times rows
- * [0, m_i), a scale that leaves the PCG iterates unchanged.)
+ * Copy rows [row0, row0 + nrows) of the last (largest) stage's sketched pair
+ * after spcg_sketch:
+ *   A  device, nrows x d row-major (leading dimension d)
+ *   b  device, nrows (may be NULL)
+ * SRHT: row t is Z[pi(t), :] with Z = H D P [X; 0] normalised by 1/sqrt(N');
+ * stage i's pair is sqrt(N'/m_i) times rows [0, m_i), a scale that leaves the
+ * PCG iterates unchanged.  CountSketch: row t is bucket t of S_K [X Y].
  */
 spcg_status spcg_export_sketch(spcg_ctx* ctx, int64_t row0, int64_t nrows,
                                double* A, double* b);
@@ -239,6 +267,16 @@ spcg_status spcg_export_precond(spcg_ctx* ctx, double* R, double* Rinv, double* 
  */
 spcg_status spcg_gram_apply(spcg_ctx* ctx, const double* A, int64_t m, int64_t lda,
                             const double* p, double* w);
+
+/*
+ * The same pass on an FP32 (dtype 1) or BF16 (dtype 2) operand, the element
+ * types the mixed-precision path streams (dtype 0 = FP64 as above).  FP32 rows
+ * accumulate in FP32 with compensated products and sums; BF16 rows in plain
+ * FP32; the products with p use p rounded to FP32.  lda * element size must
+ * be a multiple of 16 bytes.  p, w: device FP64.
+ */
+spcg_status spcg_gram_apply_typed(spcg_ctx* ctx, const void* A, int32_t dtype, int64_t m,
+                                  int64_t lda, const double* p, double* w);
 
 /*
  * Allocation-free form of spcg_gram_apply: w = A^T (A p) in one read of A,
@@ -264,6 +302,126 @@ spcg_status spcg_gram_apply(spcg_ctx* ctx, const double* A, int64_t m, int64_t l
  */
 spcg_status spcg_gram_apply_noalloc(const double* A, int64_t m, int32_t d, int64_t lda,
                                     const double* p, double* w, void* stream);
+
+/* ----- Batched solver: many independent FP32 problems, one persistent kernel ----- */
+
+/* One problem of a batch (all pointers device, caller-owned). */
+typedef struct {
+  const float* X;           /* N x d row-major FP32 in an allocation of N * ldx
+                               floats (rows are read whole), ldx*4 % 16 == 0,
+                               16-byte aligned                                    */
+  const float* Y;           /* N FP32                                              */
+  int64_t N;                /* d < N <= 2^24                                       */
+  int32_t d;                /* 1 <= d <= 256                                       */
+  int64_t ldx;
+  double* beta;             /* output, d FP64                                      */
+} spcg_problem_f32;
+
+typedef struct spcg_batch spcg_batch;
+
+/*
+ * Prepare a batch of n problems (the array is copied; the buffers it points
+ * to are borrowed until spcg_batch_destroy).  Each problem is solved by SPCG
+ * with the CountSketch initialisation (SPCG-CS, Sec. 4.3), the paper's
+ * default sizes (m_1 = 2^ceil(log2 8d) doubling to N'/2, r = 6d, a_i = 3) and
+ * the Stage II stopping rule.  One persistent kernel solves the whole batch:
+ * each CTA runs complete solves, taking problems largest first from a work
+ * queue.  Allocates the per-CTA scratch (sized by the largest problem).
+ * The problem's sketch draws use key seed + (index in the array).
+ */
+spcg_status spcg_batch_create(const spcg_problem_f32* probs, int32_t n, void* stream,
+                              spcg_batch** out);
+void spcg_batch_destroy(spcg_batch* b);
+
+/*
+ * Solve the batch (a captured CUDA graph: queue reset + the persistent
+ * kernel, re-captured when seed, tol or the tiles change).  status_out,
+ * iters_out: host arrays of n (may be NULL), in the order of the problems
+ * given to spcg_batch_create (0 ok, 4 breakdown, 5 not converged, 6 timeout);
+ * ms_out: host, device time of the graph.  Returns the first non-zero status.
+ */
+spcg_status spcg_batch_solve(spcg_batch* b, uint64_t seed, double tol, int32_t* status_out,
+                             int32_t* iters_out, double* ms_out);
+
+/* Rows per streamed chunk, as chunk bytes per width class (d <= 32, <= 64,
+ * <= 128, <= 256): 0 = 16 KB, else a multiple of 16 in [1024, 16384]. */
+spcg_status spcg_batch_set_tiles(spcg_batch* b, const int32_t* chunk_bytes4);
+
+/* The autotuner: times the batch with 4, 8 and 16 KB chunks per width class
+ * and keeps the fastest; chosen4 (host, may be NULL) receives the choice. */
+spcg_status spcg_batch_autotune(spcg_batch* b, uint64_t seed, double tol, int32_t* chosen4);
+
+/* ----- Learned schedule (spec growth line; Sec. 4.3 leaves the
+ * automatic choice of the sketch-size schedule open) ----- */
+
+/* Number of candidate schedules the model scores (25). */
+int32_t spcg_num_candidates(void);
+
+/*
+ * Candidate schedule idx (0 <= idx < 25) for an N x d problem.  Stage 1 is
+ * always the paper's (m_1 = 2^ceil(log2 8d), a_1 = 3), so that its noise
+ * estimate is available before the choice.  idx 0: no further stage.
+ * idx = 1 + 6 (g - 1) + 3 (s - 1) + (a - 2) for g in 1..4, s in 1..2,
+ * a in 2..4: stages m_1 2^s, m_1 2^{2s}, ... up to N'/2^g with a iterations
+ * each.  idx 2 (g = 1, s = 1, a = 3) is the paper's schedule.  r, tol and the
+ * limits are those of spcg_default_schedule.  Host-only.
+ */
+spcg_status spcg_candidate_schedule(int64_t N, int32_t d, int32_t idx, spcg_schedule* out);
+
+/*
+ * The model's four features after spcg_sketch (SRHT) and stage 1 (beta =
+ * the stage-1 iterate, device): log2 N, log2 d, log10(max R_ii / min R_ii),
+ * log10(||b_1 - A_1 beta||^2 / ||b_1||^2).  out4: host.
+ */
+spcg_status spcg_features(spcg_ctx* ctx, const double* beta, float* out4);
+
+/*
+ * Algorithm 1 with the schedule chosen by the model: sketch, stage 1 (paper
+ * default), features, the network's predicted log-cost of every candidate,
+ * the remaining stages of the cheapest candidate, Stage II to tol.
+ *   Wb     device, BF16 weights (layout of spcg_mlp_forward), n_out = 25;
+ *          NULL falls back to the paper's schedule, as do non-finite outputs
+ *   norm   host, 8 floats: feature means (4) then standard deviations (4)
+ *   beta   device output; choice (host, may be NULL): the candidate used
+ */
+spcg_status spcg_solve_learned(spcg_ctx* ctx, uint64_t seed, const uint16_t* Wb, int32_t n_out,
+                               const float* norm, double tol, double* beta, spcg_info* info,
+                               int32_t* choice);
+
+/*
+ * The same solve with a fixed candidate idx (0 <= idx < 25), for measuring
+ * candidate costs.  reuse_sketch = 1 keeps the context's sketch when it was
+ * made with the same seed by a previous call (X must be unchanged), so that
+ * spcg_info's stage and Stage II times are measured without a new sketch.
+ */
+spcg_status spcg_solve_candidate(spcg_ctx* ctx, uint64_t seed, int32_t idx, double tol,
+                                 int32_t reuse_sketch, double* beta, spcg_info* info);
+
+/*
+ * The MLP 4 -> 64 -> 64 -> n_out (ReLU) with BF16 weights and FP32 arithmetic.
+ * Parameter layout (n_params = 4480 + 65 n_out): W1 (64 x 4 row-major), b1
+ * (64), W2 (64 x 64), b2 (64), W3 (n_out x 64), b3 (n_out).  1 <= n_out <= 64.
+ */
+int64_t spcg_mlp_params(int32_t n_out);
+/* Floats of workspace spcg_mlp_grad needs for a batch of B samples. */
+int64_t spcg_mlp_workspace_floats(int32_t n_out, int64_t B);
+/* y (device, B x n_out) = MLP(x) for x (device, B x 4); Wb device BF16. */
+spcg_status spcg_mlp_forward(const uint16_t* Wb, int32_t n_out, const float* x, int64_t B,
+                             float* y, void* stream);
+/*
+ * Loss = mean over the batch and outputs of (MLP(x) - t)^2 and its gradient
+ * with respect to the (BF16) weights: grad (device, n_params FP32), loss
+ * (device, 1 FP32, may be NULL); workspace: device, spcg_mlp_workspace_floats.
+ * Per-block sums are added in a fixed order (reproducible).
+ */
+spcg_status spcg_mlp_grad(const uint16_t* Wb, int32_t n_out, const float* x, const float* t,
+                          int64_t B, float* grad, float* loss, float* workspace, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 master theta;
+ * writes the BF16 copy Wb.  step counts from 1. */
+spcg_status spcg_mlp_adam(float* theta, const float* grad, float* m, float* v, int64_t P,
+                          float lr, int32_t step, uint16_t* Wb, void* stream);
+/* Wb = BF16(theta), round to nearest even. */
+spcg_status spcg_mlp_to_bf16(const float* theta, int64_t P, uint16_t* Wb, void* stream);
 
 #ifdef __cplusplus
 }

@@ -73,6 +73,22 @@ def ols(X, Y):
     return solve_triangular(R, c, lower=False)
 
 
+def ols_lowmem(X, Y):
+    """beta-hat of Eq. (ols) by Householder QR without forming Q: LAPACK dgeqrf
+    on a copy of X, Q^T Y by applying the stored reflectors (dormqr), then the
+    triangular solve.  Same definition as ``ols``; one copy of X of memory."""
+    from scipy.linalg import lapack
+    from scipy.linalg import qr as sqr
+    X = np.asarray(X, dtype=np.float64)
+    (qr_raw, tau), R = sqr(np.array(X, order="F", copy=True), mode="raw", overwrite_a=True)
+    c, _, info = lapack.dormqr("L", "T", qr_raw, tau, np.asarray(Y, dtype=np.float64)[:, None].copy(order="F"),
+                               lwork=max(1, X.shape[1] * 64))
+    if info != 0:
+        raise RuntimeError("dormqr failed")
+    d = X.shape[1]
+    return solve_triangular(np.triu(R[:d, :d]), c[:d, 0], lower=False)
+
+
 def apply_precond(R, g):
     """z = (R^T R)^{-1} g = R^{-1} (R^{-T} g)."""
     u = solve_triangular(R, g, trans="T", lower=False)

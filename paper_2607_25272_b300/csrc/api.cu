@@ -48,6 +48,13 @@ static spcg_status validate_schedule(const spcg_schedule& s, int64_t N, int d) {
     if (i > 0 && s.m[i] <= s.m[i - 1]) return SPCG_E_INVALID_ARG;
   }
   if (!(s.tol > 0.0) || s.max_iters < 0 || s.max_restarts < 0) return SPCG_E_INVALID_ARG;
+  if (s.sketch != SPCG_SKETCH_SRHT && s.sketch != SPCG_SKETCH_COUNT) return SPCG_E_INVALID_ARG;
+  if (s.sketch == SPCG_SKETCH_COUNT) {
+    if (s.K < 1) return SPCG_E_INVALID_ARG;
+    for (int i = 0; i < s.K; ++i)   // buckets fold modulo m_i: powers of two
+      if (s.m[i] & (s.m[i] - 1)) return SPCG_E_INVALID_ARG;
+    if (s.r > (int64_t(1) << 31)) return SPCG_E_INVALID_ARG;
+  }
   return SPCG_OK;
 }
 
@@ -104,7 +111,8 @@ static spcg_status start_sequence(spcg_ctx* c, const PassGeom& g, const double* 
   return SPCG_OK;
 }
 
-// One PCG iteration (four launches) after start_sequence or a previous one.
+// One PCG iteration (four launches) after start_sequence or a previous one;
+// the pass multiplies by the operand g (the FP32 copy of X in mixed mode).
 static spcg_status iteration(spcg_ctx* c, const PassGeom& g, double* beta, int& cur, int& pp,
                              int& gp, int start, int check, double tau) {
   SPCG_TRY(pass_gram_iter(c, g, pp, gp, start, check, tau));
@@ -121,6 +129,20 @@ static spcg_status run_stage(spcg_ctx* c, int i, int a_i, double* beta) {
   const PassGeom& g = c->sk.geom[i];
   SPCG_TRY(launch_reset_flags(c));
   int cur = 0, pp = 0, gp = 0;
+  SPCG_TRY(start_sequence(c, g, c->sk.bK + c->sk.stage_off[i], beta, cur));
+  for (int k = 0; k < a_i; ++k) SPCG_TRY(iteration(c, g, beta, cur, pp, gp, k == 0, 0, 0.0));
+  return SPCG_OK;
+}
+
+// A stage on the first m rows of the sketched prefix (SRHT only).
+static spcg_status run_stage_m(spcg_ctx* c, int64_t m, int a_i, double* beta) {
+  PassGeom g;
+  if (c->sk.mixed)
+    SPCG_TRY(make_pass_geom_t(c->sk.AK16, m, c->d, c->sk.ldak16, DT_BF16, &g));
+  else
+    SPCG_TRY(make_pass_geom(c->sk.AK, m, c->d, c->sk.ldak, &g));
+  SPCG_TRY(launch_reset_flags(c));
+  int cur = 0, pp = 0, gp = 0;
   SPCG_TRY(start_sequence(c, g, c->sk.bK, beta, cur));
   for (int k = 0; k < a_i; ++k) SPCG_TRY(iteration(c, g, beta, cur, pp, gp, k == 0, 0, 0.0));
   return SPCG_OK;
@@ -133,7 +155,8 @@ struct RefineResult {
 static spcg_status run_refine(spcg_ctx* c, double tol, int max_iters, int max_restarts,
                               double* beta, RefineResult* res) {
   const double tau = tol / 2.0;
-  const PassGeom& g = c->gx;
+  const PassGeom& g = c->gx;                                  // true gradients: FP64 X
+  const PassGeom& gi = (c->opts.precision == SPCG_PREC_MIXED) ? c->gxf : c->gx;   // iterations
   int total = 0, restarts = 0;
   SPCG_TRY(launch_reset_flags(c));
   for (;;) {
@@ -155,7 +178,7 @@ static spcg_status run_refine(spcg_ctx* c, double tol, int max_iters, int max_re
       const int remaining = max_iters - total;
       const int chunk = remaining < 4 ? remaining : 4;
       for (int k = 0; k < chunk; ++k) {
-        SPCG_TRY(iteration(c, g, beta, cur, pp, gp, start, 1, tau));
+        SPCG_TRY(iteration(c, gi, beta, cur, pp, gp, start, 1, tau));
         start = 0;
       }
       SPCG_TRY(sync_scalars(c));
@@ -176,6 +199,7 @@ static spcg_status run_refine(spcg_ctx* c, double tol, int max_iters, int max_re
 }
 
 static void free_sketch(Sketch& s) {
+  dfree(s.AK16);
   dfree(s.gather);
   dfree(s.dest);
   dfree(s.hdest);
@@ -184,7 +208,7 @@ static void free_sketch(Sketch& s) {
   dfree(s.bK);
   dfree(s.Ahat);
   s.ready = false;
-  s.mK_alloc = s.r_alloc = 0;
+  s.rows_alloc = s.r_alloc = 0;
   s.work_bytes = 0;
   s.n_pad = 0;
 }
@@ -224,6 +248,32 @@ extern "C" spcg_status spcg_default_schedule(int64_t N, int32_t d, spcg_schedule
   out->tol = 1e-6;
   out->max_iters = 100;
   out->max_restarts = 5;
+  return SPCG_OK;
+}
+
+extern "C" spcg_status spcg_tuned_schedule(int64_t N, int32_t d, spcg_schedule* out) {
+  SPCG_TRY(spcg_default_schedule(N, d, out));
+  const int64_t n_pad = next_pow2(N);
+  int64_t m = next_pow2(16 * (int64_t)d);
+  int K = 0;
+  while (K < 7 && m < n_pad / 4) {
+    out->m[K] = m;
+    out->a[K] = 4;
+    ++K;
+    m *= 2;
+  }
+  const int64_t last = K > 0 ? out->m[K - 1] : 0;
+  if (n_pad / 4 > last && n_pad / 4 > 6 * (int64_t)d) {
+    out->m[K] = n_pad / 4;
+    out->a[K] = 4;
+    ++K;
+  }
+  for (int i = K; i < SPCG_MAX_STAGES; ++i) {
+    out->m[i] = 0;
+    out->a[i] = 0;
+  }
+  out->K = K;
+  out->r = 6 * (int64_t)d < n_pad ? 6 * (int64_t)d : n_pad;
   return SPCG_OK;
 }
 
@@ -286,7 +336,21 @@ extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, 
   if ((st = dalloc(&s.R, (size_t)d * d)) != SPCG_OK) return fail(st);
   if ((st = dalloc(&s.Rinv, (size_t)d * d)) != SPCG_OK) return fail(st);
   if ((st = dalloc(&s.RinvT, (size_t)d * d)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&s.colmax, (size_t)d + 1)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&c->mlp_x, 16)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&c->mlp_y, 64)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&c->feat_part, 2 * 128)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(&s.colshift, (size_t)d + 1)) != SPCG_OK) return fail(st);
   if ((st = make_pass_geom(c->X, N, d, c->ldx, &c->gx)) != SPCG_OK) return fail(st);
+  if (c->opts.precision != SPCG_PREC_FP64 && c->opts.precision != SPCG_PREC_MIXED)
+    return fail(SPCG_E_INVALID_ARG);
+  if (c->opts.precision == SPCG_PREC_MIXED) {
+    c->ldxf = (d + 3) & ~int64_t(3);
+    if ((st = dalloc(&c->Xf, (size_t)N * c->ldxf)) != SPCG_OK) return fail(st);
+    if (c->ldxf > d && cudaMemsetAsync(c->Xf, 0, (size_t)N * c->ldxf * 4, c->stream) != cudaSuccess)
+      return fail(SPCG_E_CUDA);
+    if ((st = make_pass_geom_t(c->Xf, N, d, c->ldxf, DT_F32, &c->gxf)) != SPCG_OK) return fail(st);
+  }
   for (auto& e : c->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(SPCG_E_CUDA);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(SPCG_E_CUDA);
@@ -303,6 +367,11 @@ extern "C" void spcg_destroy(spcg_ctx* c) {
   dfree(c->sk.R);
   dfree(c->sk.Rinv);
   dfree(c->sk.RinvT);
+  dfree(c->sk.colmax);
+  dfree(c->mlp_x);
+  dfree(c->mlp_y);
+  dfree(c->feat_part);
+  dfree(c->sk.colshift);
   PcgBuffers& pb = c->pb;
   dfree(pb.partials);
   dfree(pb.w);
@@ -318,6 +387,8 @@ extern "C" void spcg_destroy(spcg_ctx* c) {
   dfree(c->beta_work);
   dfree(c->scal);
   dfree(c->X_own);
+  dfree(c->Xf);
+  dfree(c->sk.AK16);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (int i = 0; i < c->prof_cap; ++i)
@@ -348,8 +419,16 @@ extern "C" spcg_status spcg_sketch(spcg_ctx* c, uint64_t seed, const spcg_schedu
     s.n_pad = n_pad;
   }
   s.nbits = nbits;
+  const bool cs = sc.sketch == SPCG_SKETCH_COUNT;
+  // stage storage: SRHT stages share one prefix; CountSketch stages are separate
+  int64_t rows = 0;
+  for (int i = 0; i < sc.K; ++i) {
+    s.stage_off[i] = cs ? rows : 0;
+    rows = cs ? rows + sc.m[i] : mK;
+  }
   const bool multipass = nbits > 12;
-  const size_t work_bytes = multipass ? (size_t)n_pad * (d + 1) * 8 : 0;
+  size_t work_bytes = multipass ? (size_t)n_pad * (d + 1) * 8 : 0;
+  if (cs) work_bytes = (size_t)(mK + sc.r) * (d + 1) * 8;   // int64 buckets of S_K and S-hat
   if (work_bytes > s.work_bytes) {
     dfree(s.work);
     SPCG_TRY(dalloc((unsigned char**)&s.work, work_bytes));
@@ -357,13 +436,19 @@ extern "C" spcg_status spcg_sketch(spcg_ctx* c, uint64_t seed, const spcg_schedu
   }
   s.ldw = d + 1;
   s.ldak = (d + 1) & ~int64_t(1);
-  if (mK > s.mK_alloc) {
+  s.ldak16 = (d + 7) & ~int64_t(7);
+  const bool mixed = (c->opts.precision == SPCG_PREC_MIXED);
+  if (rows > s.rows_alloc || mixed != s.mixed) {
     dfree(s.AK);
+    dfree(s.AK16);
     dfree(s.bK);
-    SPCG_TRY(dalloc(&s.AK, (size_t)mK * s.ldak));
-    SPCG_TRY(dalloc(&s.bK, (size_t)mK));
-    s.mK_alloc = mK;
+    s.rows_alloc = 0;
+    SPCG_TRY(dalloc(&s.bK, (size_t)rows));
+    if (mixed) SPCG_TRY(dalloc(&s.AK16, (size_t)rows * s.ldak16));
+    else SPCG_TRY(dalloc(&s.AK, (size_t)rows * s.ldak));
+    s.rows_alloc = rows;
   }
+  s.mixed = mixed;
   if (sc.r > s.r_alloc) {
     dfree(s.Ahat);
     SPCG_TRY(dalloc(&s.Ahat, (size_t)sc.r * d));
@@ -371,12 +456,24 @@ extern "C" spcg_status spcg_sketch(spcg_ctx* c, uint64_t seed, const spcg_schedu
   }
   s.seed = seed;
   s.sched = sc;
-  if (s.ldak > d && mK > 0)   // padding columns of the prefix stay zero
-    SPCG_CK(cudaMemsetAsync(s.AK, 0, (size_t)mK * s.ldak * 8, c->stream));
-  for (int i = 0; i < sc.K; ++i) SPCG_TRY(make_pass_geom(s.AK, sc.m[i], d, s.ldak, &s.geom[i]));
+  if (!s.mixed && s.ldak > d && rows > 0)   // padding columns of the stage rows stay zero
+    SPCG_CK(cudaMemsetAsync(s.AK, 0, (size_t)rows * s.ldak * 8, c->stream));
+  if (s.mixed && s.ldak16 > d && rows > 0)
+    SPCG_CK(cudaMemsetAsync(s.AK16, 0, (size_t)rows * s.ldak16 * 2, c->stream));
+  for (int i = 0; i < sc.K; ++i) {
+    if (s.mixed)
+      SPCG_TRY(make_pass_geom_t(reinterpret_cast<uint16_t*>(s.AK16) + s.stage_off[i] * s.ldak16,
+                                sc.m[i], d, s.ldak16, DT_BF16, &s.geom[i]));
+    else
+      SPCG_TRY(make_pass_geom(s.AK + s.stage_off[i] * s.ldak, sc.m[i], d, s.ldak, &s.geom[i]));
+  }
   SPCG_TRY(launch_reset_flags(c));
-  SPCG_TRY(launch_sketch_maps(c));
-  SPCG_TRY(launch_transform(c));
+  if (cs) {
+    SPCG_TRY(launch_countsketch(c));
+  } else {
+    SPCG_TRY(launch_sketch_maps(c));
+    SPCG_TRY(launch_transform(c));
+  }
   SPCG_TRY(launch_precond_factor(c));
   SPCG_TRY(sync_scalars(c));
   s.ready = true;
@@ -395,6 +492,7 @@ extern "C" spcg_status spcg_refine(spcg_ctx* c, double tol, int32_t max_iters, d
                                    int32_t* iters_out) {
   if (!c || !beta || !(tol > 0.0) || max_iters < 0) return SPCG_E_INVALID_ARG;
   if (!c->sk.ready) return SPCG_E_STATE;
+  if (c->opts.precision == SPCG_PREC_MIXED) SPCG_TRY(launch_to_f32(c));
   RefineResult rr;
   spcg_status st = run_refine(c, tol, max_iters, c->sk.sched.max_restarts, beta, &rr);
   if (iters_out) *iters_out = rr.iters;
@@ -410,6 +508,7 @@ extern "C" spcg_status spcg_solve(spcg_ctx* c, uint64_t seed, const spcg_schedul
   c->prof_ms = 0.0;
   SPCG_CK(cudaEventRecord(c->ev[0], c->stream));
   SPCG_TRY(spcg_sketch(c, seed, sched));
+  if (c->opts.precision == SPCG_PREC_MIXED) SPCG_TRY(launch_to_f32(c));
   SPCG_CK(cudaEventRecord(c->ev[1], c->stream));
   const spcg_schedule& sc = c->sk.sched;
   SPCG_CK(cudaMemsetAsync(c->beta_work, 0, (size_t)c->d * 8, c->stream));
@@ -454,12 +553,7 @@ extern "C" spcg_status spcg_export_sketch(spcg_ctx* c, int64_t row0, int64_t nro
   const int64_t mK = s.sched.K > 0 ? s.sched.m[s.sched.K - 1] : 0;
   if (row0 + nrows > mK) return SPCG_E_INVALID_ARG;
   if (nrows == 0) return SPCG_OK;
-  if (A)
-    SPCG_CK(cudaMemcpy2DAsync(A, (size_t)c->d * 8, s.AK + row0 * s.ldak, (size_t)s.ldak * 8,
-                              (size_t)c->d * 8, nrows, cudaMemcpyDeviceToDevice, c->stream));
-  if (b)
-    SPCG_CK(cudaMemcpyAsync(b, s.bK + row0, (size_t)nrows * 8, cudaMemcpyDeviceToDevice,
-                            c->stream));
+  SPCG_TRY(launch_export_rows(c, row0, nrows, A, b));
   SPCG_CK(cudaStreamSynchronize(c->stream));
   return SPCG_OK;
 }
@@ -481,8 +575,9 @@ extern "C" spcg_status spcg_export_precond(spcg_ctx* c, double* R, double* Rinv,
   if (Rinv) SPCG_CK(cudaMemcpyAsync(Rinv, c->sk.Rinv, dd, cudaMemcpyDeviceToDevice, c->stream));
   if (Ahat) {
     // Ahat is reduced in place by the QR; only R survives.  Re-run the
-    // transform into it when an export is asked for.
-    SPCG_TRY(launch_transform(c));
+    // sketch into it when an export is asked for.
+    if (c->sk.sched.sketch == SPCG_SKETCH_COUNT) SPCG_TRY(launch_countsketch(c));
+    else SPCG_TRY(launch_transform(c));
     k_colmajor_to_rowmajor<<<256, 256, 0, c->stream>>>(c->sk.Ahat, c->sk.sched.r, c->d, Ahat);
     SPCG_CK(cudaGetLastError());
     // restore the factorised state expected by later calls
@@ -506,4 +601,170 @@ extern "C" spcg_status spcg_gram_apply(spcg_ctx* c, const double* A, int64_t m, 
   SPCG_TRY(pass_gram_plain(c, g, p));
   SPCG_TRY(launch_reduce(c, w, nullptr));
   return sync_scalars(c);
+}
+
+extern "C" spcg_status spcg_gram_apply_typed(spcg_ctx* c, const void* A, int32_t dtype, int64_t m,
+                                             int64_t lda, const double* p, double* w) {
+  if (!c || !p || !w || m < 0 || dtype < 0 || dtype > 2) return SPCG_E_INVALID_ARG;
+  if (m == 0) {
+    SPCG_CK(cudaMemsetAsync(w, 0, (size_t)c->d * 8, c->stream));
+    SPCG_CK(cudaStreamSynchronize(c->stream));
+    return SPCG_OK;
+  }
+  if (!A) return SPCG_E_INVALID_ARG;
+  PassGeom g;
+  SPCG_TRY(make_pass_geom_t(A, m, c->d, lda, dtype, &g));
+  SPCG_TRY(launch_reset_flags(c));
+  SPCG_TRY(pass_gram_plain(c, g, p));
+  SPCG_TRY(launch_reduce(c, w, nullptr));
+  return sync_scalars(c);
+}
+
+// ---------------------------------------------------------------------------
+// Learned schedule: candidates, features, and the solve that uses the model.
+// ---------------------------------------------------------------------------
+namespace spcg {
+spcg_status mlp_forward_launch(const void* Wb, int nout, const float* x, int64_t B, float* y,
+                               cudaStream_t st);
+spcg_status launch_features(spcg_ctx* c, const double* beta, float* dev_out2);
+}
+
+extern "C" int32_t spcg_num_candidates(void) { return 25; }
+
+extern "C" spcg_status spcg_candidate_schedule(int64_t N, int32_t d, int32_t idx,
+                                               spcg_schedule* out) {
+  if (idx < 0 || idx >= 25) return SPCG_E_INVALID_ARG;
+  SPCG_TRY(spcg_default_schedule(N, d, out));
+  if (out->K == 0) return SPCG_OK;
+  const int64_t n_pad = next_pow2(N);
+  const int64_t m1 = out->m[0];
+  int K = 1;
+  out->a[0] = 3;
+  if (idx > 0) {
+    const int g = 1 + (idx - 1) / 6, rem = (idx - 1) % 6, sgrow = 1 + rem / 3, a = 2 + rem % 3;
+    const int64_t top = n_pad >> g;
+    for (int64_t m = m1 << sgrow; m <= top && K < SPCG_MAX_STAGES; m <<= sgrow) {
+      out->m[K] = m;
+      out->a[K] = a;
+      ++K;
+    }
+  }
+  for (int i = K; i < SPCG_MAX_STAGES; ++i) {
+    out->m[i] = 0;
+    out->a[i] = 0;
+  }
+  out->K = K;
+  return SPCG_OK;
+}
+
+extern "C" spcg_status spcg_features(spcg_ctx* c, const double* beta, float* out4) {
+  if (!c || !beta || !out4) return SPCG_E_INVALID_ARG;
+  if (!c->sk.ready || c->sk.sched.sketch != SPCG_SKETCH_SRHT || c->sk.sched.K < 1)
+    return SPCG_E_STATE;
+  SPCG_TRY(launch_features(c, beta, c->mlp_x + 2));
+  float f2[2];
+  SPCG_CK(cudaMemcpyAsync(f2, c->mlp_x + 2, sizeof(f2), cudaMemcpyDeviceToHost, c->stream));
+  SPCG_CK(cudaStreamSynchronize(c->stream));
+  out4[0] = (float)log2((double)c->N);
+  out4[1] = (float)log2((double)c->d);
+  out4[2] = f2[0];
+  out4[3] = f2[1];
+  return SPCG_OK;
+}
+
+// Sketch (or reuse the context's sketch of the same seed), stage 1, then the
+// candidate `force_idx` (>= 0) or the one the model scores cheapest.
+static spcg_status solve_choice(spcg_ctx* c, uint64_t seed, const uint16_t* Wb, int32_t n_out,
+                                const float* norm, double tol, int force_idx, int reuse,
+                                double* beta, spcg_info* info, int32_t* choice) {
+  if (!c || !beta || !(tol > 0.0)) return SPCG_E_INVALID_ARG;
+  if (info) memset(info, 0, sizeof(*info));
+  const int paper = 2;   // candidate index of the paper's schedule
+  spcg_schedule sc;
+  SPCG_TRY(spcg_default_schedule(c->N, c->d, &sc));
+  sc.tol = tol;
+  c->n_launch = c->n_pass = 0;
+  c->pass_bytes = 0;
+  c->prof_ms = 0.0;
+  SPCG_CK(cudaEventRecord(c->ev[0], c->stream));
+  const bool have = reuse && c->sk.ready && c->sk.seed == seed &&
+                    c->sk.sched.sketch == SPCG_SKETCH_SRHT && c->sk.sched.K == sc.K &&
+                    (sc.K == 0 || c->sk.sched.m[sc.K - 1] == sc.m[sc.K - 1]);
+  if (!have) {
+    SPCG_TRY(spcg_sketch(c, seed, &sc));   // the prefix holds N'/2 rows: every candidate fits
+    if (c->opts.precision == SPCG_PREC_MIXED) SPCG_TRY(launch_to_f32(c));
+  }
+  SPCG_CK(cudaEventRecord(c->ev[1], c->stream));
+  SPCG_CK(cudaMemsetAsync(c->beta_work, 0, (size_t)c->d * 8, c->stream));
+  int idx = paper;
+  spcg_schedule cand = sc;
+  if (sc.K > 0) {
+    SPCG_TRY(run_stage(c, 0, 3, c->beta_work));
+    if (force_idx >= 0) {
+      idx = force_idx;
+    } else if (Wb && norm && n_out == 25) {
+      float f[4];
+      SPCG_TRY(spcg_features(c, c->beta_work, f));
+      float xn[4];
+      for (int k = 0; k < 4; ++k) xn[k] = (f[k] - norm[k]) / norm[4 + k];
+      SPCG_CK(cudaMemcpyAsync(c->mlp_x, xn, sizeof(xn), cudaMemcpyHostToDevice, c->stream));
+      SPCG_TRY(mlp_forward_launch(Wb, n_out, c->mlp_x, 1, c->mlp_y, c->stream));
+      c->n_launch += 1;
+      float y[25];
+      SPCG_CK(cudaMemcpyAsync(y, c->mlp_y, sizeof(y), cudaMemcpyDeviceToHost, c->stream));
+      SPCG_CK(cudaStreamSynchronize(c->stream));
+      bool ok = true;
+      int best = 0;
+      for (int k = 0; k < 25; ++k) {
+        if (!isfinite(y[k])) ok = false;
+        if (y[k] < y[best]) best = k;
+      }
+      if (ok) idx = best;
+    }
+    SPCG_TRY(spcg_candidate_schedule(c->N, c->d, idx, &cand));
+    for (int i = 1; i < cand.K; ++i) SPCG_TRY(run_stage_m(c, cand.m[i], cand.a[i], c->beta_work));
+  }
+  SPCG_TRY(sync_scalars(c));
+  SPCG_CK(cudaEventRecord(c->ev[2], c->stream));
+  RefineResult rr;
+  spcg_status st = run_refine(c, tol, sc.max_iters, sc.max_restarts, c->beta_work, &rr);
+  SPCG_CK(cudaEventRecord(c->ev[3], c->stream));
+  SPCG_CK(cudaMemcpyAsync(beta, c->beta_work, (size_t)c->d * 8, cudaMemcpyDeviceToDevice,
+                          c->stream));
+  SPCG_CK(cudaStreamSynchronize(c->stream));
+  SPCG_TRY(prof_collect(c));
+  if (choice) *choice = idx;
+  if (info) {
+    info->K = cand.K;
+    for (int i = 0; i < cand.K; ++i) info->stage_iters[i] = cand.a[i];
+    info->refine_iters = rr.iters;
+    info->restarts = rr.restarts;
+    info->converged = rr.converged;
+    info->sqrt_gamma = c->host_scal.sqrt_gamma;
+    info->norm_R_beta = c->host_scal.norm_rb;
+    info->bytes_pass = c->pass_bytes;
+    info->pass_launches = (int32_t)c->n_pass;
+    info->launches = (int32_t)c->n_launch;
+    info->pass_ms = c->prof_ms;
+    float ms;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+    info->ms_sketch = ms;
+    cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
+    info->ms_stages = ms;
+    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+    info->ms_refine = ms;
+  }
+  return st;
+}
+
+extern "C" spcg_status spcg_solve_learned(spcg_ctx* c, uint64_t seed, const uint16_t* Wb,
+                                          int32_t n_out, const float* norm, double tol,
+                                          double* beta, spcg_info* info, int32_t* choice) {
+  return solve_choice(c, seed, Wb, n_out, norm, tol, -1, 0, beta, info, choice);
+}
+
+extern "C" spcg_status spcg_solve_candidate(spcg_ctx* c, uint64_t seed, int32_t idx, double tol,
+                                            int32_t reuse_sketch, double* beta, spcg_info* info) {
+  if (idx < 0 || idx >= 25) return SPCG_E_INVALID_ARG;
+  return solve_choice(c, seed, nullptr, 0, nullptr, tol, idx, reuse_sketch, beta, info, nullptr);
 }

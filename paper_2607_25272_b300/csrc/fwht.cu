@@ -1,45 +1,132 @@
 // The nested SRHT transform (Sec. 2.2): Z = H D P [X Y; 0] over N' = 2^n
-// padded rows, H the normalised Sylvester Walsh-Hadamard matrix.
+// padded rows, H the Sylvester Walsh-Hadamard matrix.
 //
-// H_{N'} factors over groups of index bits: a pass that owns bits
+// Arithmetic.  H has entries +-1, so the transform is additions only.  Each
+// column c is converted once to 64-bit fixed point, q = round(x 2^{s_c}),
+// with s_c chosen from the column's largest magnitude so that no partial
+// sum of N' terms can reach 2^62; every butterfly is then an exact integer
+// add, and the only rounding is the conversion in and out (error at most
+// half a quantum 2^{-s_c} per input element, and one rounding to FP64 per
+// output).  This keeps the B300's slow FP64 pipe out of the transform.
+//
+// Passes.  H_{N'} factors over groups of index bits: a pass that owns bits
 // [s, s + b) runs the 2^b-point transform on every set of rows that differ
-// only in those bits.  Each CTA stages one such set (2^b rows, rows 2^s
-// apart) for a slab of TC adjacent columns in shared memory, runs the b
-// butterfly levels there and writes the slab back.  The first pass fuses
-// the signed row gather (D P), the last pass fuses the 1/sqrt(N') scale and
-// the scatter of the rows of I_K (to their position in pi order) and of
-// I-hat (scaled by sqrt(N'/r), column-major for the QR).  Y is column d.
+// only in those bits.  Each CTA stages one such set (2^b rows, 2^s apart)
+// for a slab of TC adjacent columns.  Inside the tile, threads take 2^g
+// values of one column into registers and run g butterfly levels there
+// (g <= 4), so a 10-level tile needs three register rounds and four passes
+// over shared memory.  The first pass fuses the signed row gather (D P) and
+// the conversion to fixed point; the last pass converts back and scatters
+// the rows of I_K (to their position in pi order) and of I-hat (scaled by
+// 1/sqrt(r), column-major for the QR).  Y is column d.
+//
+// Scale.  The stage rows are stored as H' D P X' with the unnormalised +-1
+// matrix H' (PCG iterates do not change under a joint scaling of A and b);
+// S-hat X = sqrt(N'/r) H D P X' [I-hat] = H' D P X' [I-hat] / sqrt(r).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.hpp"
 
 namespace spcg {
 
+// ---- exact conversions between FP64 and 64-bit fixed point ----
+// q = x 2^s rounded half away from zero (subnormal inputs count as zero).
+__device__ __forceinline__ long long to_fixed(double x, int s) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0;
+  const unsigned long long mant = (unsigned long long)(b & 0xFFFFFFFFFFFFFll) | (1ull << 52);
+  const int sh = e - 1075 + s;   // x 2^s = mant 2^sh
+  unsigned long long q;
+  if (sh >= 0) q = mant << sh;   // the scale bound keeps this below 2^62
+  else if (sh > -64) q = (mant + (1ull << (-sh - 1))) >> (-sh);
+  else q = 0;
+  return (b < 0) ? -(long long)q : (long long)q;
+}
+
+// q 2^{-s} rounded to nearest even (results below the normal range flush to 0).
+__device__ __forceinline__ double from_fixed(long long q, int s) {
+  if (q == 0) return 0.0;
+  const unsigned long long sign = q < 0 ? 1ull : 0ull;
+  const unsigned long long v = sign ? (unsigned long long)(-q) : (unsigned long long)q;
+  int top = 63 - __clzll((long long)v);
+  unsigned long long m;
+  if (top <= 52) {
+    m = v << (52 - top);
+  } else {
+    const int drop = top - 52;
+    m = v >> drop;
+    const unsigned long long rem = v & ((1ull << drop) - 1), half = 1ull << (drop - 1);
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m == (1ull << 53)) {
+      m >>= 1;
+      ++top;
+    }
+  }
+  const int biased = top - s + 1023;
+  if (biased <= 0) return 0.0;
+  const unsigned long long bits =
+      (sign << 63) | ((unsigned long long)biased << 52) | (m & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
+// Per-column largest magnitude (as IEEE bit patterns: for non-negative
+// doubles the integer order is the numeric order, so atomicMax is exact).
+__global__ void __launch_bounds__(256) k_colmax(const double* __restrict__ X, int64_t ldx,
+                                                const double* __restrict__ Y, int64_t N, int d,
+                                                unsigned long long* __restrict__ colmax) {
+  const int C = d + 1;
+  for (int c0 = 0; c0 < C; c0 += blockDim.x) {
+    const int c = c0 + threadIdx.x;
+    unsigned long long mx = 0;
+    if (c < C) {
+      for (int64_t i = blockIdx.x; i < N; i += gridDim.x) {
+        const double v = (c < d) ? X[i * ldx + c] : Y[i];
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+        mx = b > mx ? b : mx;
+      }
+      atomicMax(colmax + c, mx);
+    }
+  }
+}
+
+// s_c = 61 - n - E_c with 2^{E_c} <= max_c < 2^{E_c+1}: every partial sum of
+// N' <= 2^n terms stays below 2^62 in magnitude.
+__global__ void k_colscale(const unsigned long long* __restrict__ colmax, int C, int nbits,
+                           int* __restrict__ shift) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    const unsigned long long b = colmax[c];
+    const int e = (int)((b >> 52) & 0x7FF);
+    shift[c] = (e == 0) ? 0 : 61 - nbits - (e - 1023);
+  }
+}
+
 struct FwhtArgs {
-  // source of the first pass
   const double* X;
   int64_t ldx;
   const double* Y;
   int64_t N;
   const uint32_t* gather;
-  // work buffer
-  double* W;
+  const int* shift;      // per-column fixed-point scale exponent
+  long long* W;          // work buffer N' x ldw (multi-pass only)
   int64_t ldw;
-  int C;             // d + 1 columns (Y last)
+  int C;                 // d + 1 columns (Y last)
   int d;
-  int nbits;         // log2 N'
-  int shift;         // low bit of this pass
+  int shift_lo;          // low index bit of this pass
   int first, last;
   int ncoltiles;
-  // scatter of the last pass
   const int32_t* dest;
   const int32_t* hdest;
-  double* AK;
+  double* AK;            // FP64 prefix (or null)
   int64_t ldak;
+  __nv_bfloat16* AK16;   // BF16 prefix (or null)
+  int64_t ldak16;
   double* bK;
-  double* Ahat;      // column-major, ld = r
+  double* Ahat;          // column-major, ld = r
   int64_t r;
-  double scale;      // 1/sqrt(N')
-  double hat_scale;  // sqrt(N'/r)
+  double hat_scale;      // 1/sqrt(r)
 };
 
 template <int LOGL>
@@ -47,95 +134,145 @@ struct FwhtShape {
   static constexpr int L = 1 << LOGL;
   static constexpr int TC = (L <= 1024) ? 16 : (L == 2048 ? 8 : 4);
   static constexpr int THREADS = 512;
-  static constexpr size_t SMEM = (size_t)L * TC * sizeof(double) + (size_t)L * 3 * sizeof(int32_t);
+  static constexpr int ROUNDS = (LOGL + 3) / 4;
+  static constexpr size_t SMEM = (size_t)L * TC * 8 + (size_t)L * 3 * 4 + (size_t)TC * 4;
 };
+
+// g-level butterfly on 2^g registers (index bits 0..g-1 of the register index).
+template <int G>
+__device__ __forceinline__ void bfly(long long (&v)[1 << G]) {
+#pragma unroll
+  for (int b = 0; b < G; ++b) {
+#pragma unroll
+    for (int k = 0; k < (1 << G); ++k) {
+      if (k & (1 << b)) continue;
+      const long long x = v[k], y = v[k | (1 << b)];
+      v[k] = x + y;
+      v[k | (1 << b)] = x - y;
+    }
+  }
+}
+
+template <int LOGL>
+__device__ __forceinline__ int round_levels(int rnd) {
+  constexpr int R = FwhtShape<LOGL>::ROUNDS;
+  return LOGL / R + (rnd < LOGL % R ? 1 : 0);
+}
+
+// One register round: g levels starting at tile-row bit `lev`.  Values come
+// from global memory in the first round and go to global memory in the last.
+template <int LOGL, int G>
+__device__ __forceinline__ void do_round(const FwhtArgs& a, long long* tile, const int32_t* gmap,
+                                         const int32_t* dmap, const int32_t* hmap,
+                                         const int* sh, int lev, bool from_global, bool to_global,
+                                         int c0, int64_t low, int64_t high) {
+  using S = FwhtShape<LOGL>;
+  constexpr int L = S::L, TC = S::TC, NT = S::THREADS, GN = 1 << G;
+  const int h = 1 << lev;
+  for (int q = threadIdx.x; q < (L / GN) * TC; q += NT) {
+    const int c = q % TC, gi = q / TC;
+    const int t0 = (gi & (h - 1)) | ((gi >> lev) << (lev + G));
+    const int col = c0 + c;
+    long long v[GN];
+#pragma unroll
+    for (int k = 0; k < GN; ++k) {
+      const int t = t0 + k * h;
+      long long x = 0;
+      if (from_global) {
+        if (col < a.C) {
+          if (a.first) {
+            const uint32_t gm = (uint32_t)gmap[t];
+            const int64_t src = (int64_t)(gm & 0x7FFFFFFFu);
+            if (src < a.N) {
+              const double xv = (col < a.d) ? a.X[src * a.ldx + col] : a.Y[src];
+              x = to_fixed(xv, sh[c]);
+              if (gm & 0x80000000u) x = -x;
+            }
+          } else {
+            const int64_t j = low | ((int64_t)t << a.shift_lo) | (high << (a.shift_lo + LOGL));
+            x = a.W[j * a.ldw + col];
+          }
+        }
+      } else {
+        x = tile[t * TC + c];
+      }
+      v[k] = x;
+    }
+    bfly<G>(v);
+#pragma unroll
+    for (int k = 0; k < GN; ++k) {
+      const int t = t0 + k * h;
+      if (!to_global) {
+        tile[t * TC + c] = v[k];
+      } else if (col < a.C) {
+        if (!a.last) {
+          const int64_t j = low | ((int64_t)t << a.shift_lo) | (high << (a.shift_lo + LOGL));
+          a.W[j * a.ldw + col] = v[k];
+        } else {
+          const int32_t dst = dmap[t], hd = hmap[t];
+          if (dst >= 0 || hd >= 0) {
+            const double z = from_fixed(v[k], sh[c]);
+            if (dst >= 0) {
+              if (col < a.d) {
+                if (a.AK) a.AK[(int64_t)dst * a.ldak + col] = z;
+                if (a.AK16) a.AK16[(int64_t)dst * a.ldak16 + col] = __double2bfloat16(z);
+              } else {
+                a.bK[dst] = z;
+              }
+            }
+            if (hd >= 0 && col < a.d) a.Ahat[(int64_t)col * a.r + hd] = z * a.hat_scale;
+          }
+        }
+      }
+    }
+  }
+}
 
 template <int LOGL>
 __global__ void __launch_bounds__(512) k_fwht_pass(const FwhtArgs a) {
   using S = FwhtShape<LOGL>;
-  constexpr int L = S::L, TC = S::TC, NT = S::THREADS;
+  constexpr int L = S::L, TC = S::TC, NT = S::THREADS, R = S::ROUNDS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* tile = reinterpret_cast<double*>(smem_raw);
-  int32_t* gmap = reinterpret_cast<int32_t*>(tile + (size_t)L * TC);  // gather (first pass)
-  int32_t* dmap = gmap + L;                                             // dest (last pass)
-  int32_t* hmap = dmap + L;                                             // hdest (last pass)
+  long long* tile = reinterpret_cast<long long*>(smem_raw);
+  int32_t* gmap = reinterpret_cast<int32_t*>(tile + (size_t)L * TC);
+  int32_t* dmap = gmap + L;
+  int32_t* hmap = dmap + L;
+  int* sh = hmap + L;
 
   const int64_t blk = blockIdx.x;
   const int ct = (int)(blk % a.ncoltiles);
   const int64_t base = blk / a.ncoltiles;
   const int c0 = ct * TC;
-  const int64_t low = base & ((int64_t(1) << a.shift) - 1);
-  const int64_t high = base >> a.shift;
-  // global row of tile row t
+  const int64_t low = base & ((int64_t(1) << a.shift_lo) - 1);
+  const int64_t high = base >> a.shift_lo;
   auto grow = [&](int t) -> int64_t {
-    return low | ((int64_t)t << a.shift) | (high << (a.shift + LOGL));
+    return low | ((int64_t)t << a.shift_lo) | (high << (a.shift_lo + LOGL));
   };
-
   const int tid = threadIdx.x;
-  if (a.first) {
+  for (int c = tid; c < TC; c += NT) sh[c] = (c0 + c < a.C) ? a.shift[c0 + c] : 0;
+  if (a.first)
     for (int t = tid; t < L; t += NT) gmap[t] = (int32_t)a.gather[grow(t)];
-  }
-  if (a.last) {
+  if (a.last)
     for (int t = tid; t < L; t += NT) {
       const int64_t j = grow(t);
       dmap[t] = a.dest[j];
       hmap[t] = a.hdest[j];
     }
-  }
   __syncthreads();
 
-  // load
-  for (int e = tid; e < L * TC; e += NT) {
-    const int t = e / TC, c = e % TC;
-    const int col = c0 + c;
-    double v = 0.0;
-    if (col < a.C) {
-      if (a.first) {
-        const uint32_t gm = (uint32_t)gmap[t];
-        const int64_t src = (int64_t)(gm & 0x7FFFFFFFu);
-        if (src < a.N) {
-          v = (col < a.d) ? a.X[src * a.ldx + col] : a.Y[src];
-          if (gm & 0x80000000u) v = -v;
-        }
-      } else {
-        v = a.W[grow(t) * a.ldw + col];
-      }
-    }
-    tile[e] = v;
-  }
-  __syncthreads();
-
-  // radix-2 butterflies over the LOGL bits of the tile row index
+  int lev = 0;
 #pragma unroll 1
-  for (int h = 1; h < L; h <<= 1) {
-    for (int q = tid; q < (L / 2) * TC; q += NT) {
-      const int c = q % TC, pr = q / TC;
-      const int t = (pr / h) * 2 * h + (pr % h);
-      const double x = tile[t * TC + c], y = tile[(t + h) * TC + c];
-      tile[t * TC + c] = x + y;
-      tile[(t + h) * TC + c] = x - y;
+  for (int rnd = 0; rnd < R; ++rnd) {
+    const int g = round_levels<LOGL>(rnd);
+    const bool fg = (rnd == 0), tg = (rnd == R - 1);
+    switch (g) {
+      case 1: do_round<LOGL, 1>(a, tile, gmap, dmap, hmap, sh, lev, fg, tg, c0, low, high); break;
+      case 2: do_round<LOGL, 2>(a, tile, gmap, dmap, hmap, sh, lev, fg, tg, c0, low, high); break;
+      case 3: do_round<LOGL, 3>(a, tile, gmap, dmap, hmap, sh, lev, fg, tg, c0, low, high); break;
+      default: do_round<LOGL, 4>(a, tile, gmap, dmap, hmap, sh, lev, fg, tg, c0, low, high); break;
     }
+    lev += g;
     __syncthreads();
-  }
-
-  // store
-  for (int e = tid; e < L * TC; e += NT) {
-    const int t = e / TC, c = e % TC;
-    const int col = c0 + c;
-    if (col >= a.C) continue;
-    double v = tile[e];
-    if (!a.last) {
-      a.W[grow(t) * a.ldw + col] = v;
-    } else {
-      v *= a.scale;
-      const int32_t dst = dmap[t];
-      if (dst >= 0) {
-        if (col < a.d) a.AK[(int64_t)dst * a.ldak + col] = v;
-        else a.bK[dst] = v;
-      }
-      const int32_t hd = hmap[t];
-      if (hd >= 0 && col < a.d) a.Ahat[(int64_t)col * a.r + hd] = v * a.hat_scale;
-    }
   }
 }
 
@@ -144,11 +281,10 @@ static spcg_status launch_one(const FwhtArgs& a, int64_t nbases, cudaStream_t st
   using S = FwhtShape<LOGL>;
   FwhtArgs b = a;
   b.ncoltiles = (a.C + S::TC - 1) / S::TC;
-  const size_t smem = S::SMEM;
   SPCG_CK(cudaFuncSetAttribute(k_fwht_pass<LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
+                               (int)S::SMEM));
   const int64_t nblk = nbases * b.ncoltiles;
-  k_fwht_pass<LOGL><<<(unsigned)nblk, S::THREADS, smem, st>>>(b);
+  k_fwht_pass<LOGL><<<(unsigned)nblk, S::THREADS, S::SMEM, st>>>(b);
   SPCG_CK(cudaGetLastError());
   return SPCG_OK;
 }
@@ -178,8 +314,26 @@ int fwht_pass_plan(int n, int* logl) {
   return passes;
 }
 
+// Per-column fixed-point scales: sums of up to 2^nbits terms stay below 2^62.
+spcg_status launch_colscales(spcg_ctx* c) {
+  Sketch& s = c->sk;
+  const int C = c->d + 1;
+  SPCG_CK(cudaMemsetAsync(s.colmax, 0, (size_t)C * sizeof(unsigned long long), c->stream));
+  int cg = (int)((c->N + 63) / 64);
+  if (cg > 4 * c->num_sms) cg = 4 * c->num_sms;
+  if (cg < 1) cg = 1;
+  k_colmax<<<cg, 256, 0, c->stream>>>(c->X, c->ldx, c->Y, c->N, c->d, s.colmax);
+  SPCG_CK(cudaGetLastError());
+  k_colscale<<<(C + 255) / 256, 256, 0, c->stream>>>(s.colmax, C, s.nbits, s.colshift);
+  SPCG_CK(cudaGetLastError());
+  c->n_launch += 2;
+  return SPCG_OK;
+}
+
 spcg_status launch_transform(spcg_ctx* c) {
   Sketch& s = c->sk;
+  const int C = c->d + 1;
+  SPCG_TRY(launch_colscales(c));
   int logl[8];
   const int passes = fwht_pass_plan(s.nbits, logl);
   FwhtArgs a{};
@@ -188,23 +342,24 @@ spcg_status launch_transform(spcg_ctx* c) {
   a.Y = c->Y;
   a.N = c->N;
   a.gather = s.gather;
-  a.W = s.work;
+  a.shift = s.colshift;
+  a.W = reinterpret_cast<long long*>(s.work);
   a.ldw = s.ldw;
-  a.C = c->d + 1;
+  a.C = C;
   a.d = c->d;
-  a.nbits = s.nbits;
   a.dest = s.dest;
   a.hdest = s.hdest;
-  a.AK = s.AK;
+  a.AK = s.mixed ? nullptr : s.AK;
   a.ldak = s.ldak;
+  a.AK16 = s.mixed ? reinterpret_cast<__nv_bfloat16*>(s.AK16) : nullptr;
+  a.ldak16 = s.ldak16;
   a.bK = s.bK;
   a.Ahat = s.Ahat;
   a.r = s.sched.r;
-  a.scale = 1.0 / sqrt((double)s.n_pad);
-  a.hat_scale = sqrt((double)s.n_pad / (double)s.sched.r);
+  a.hat_scale = 1.0 / sqrt((double)s.sched.r);
   int shift = 0;
   for (int p = 0; p < passes; ++p) {
-    a.shift = shift;
+    a.shift_lo = shift;
     a.first = (p == 0);
     a.last = (p == passes - 1);
     const int64_t nbases = s.n_pad >> logl[p];
@@ -212,6 +367,58 @@ spcg_status launch_transform(spcg_ctx* c) {
     c->n_launch += 1;
     shift += logl[p];
   }
+  return SPCG_OK;
+}
+
+// Rows [row0, row0 + n) of the prefix, scaled to Z = H D P X' (normalised H).
+__global__ void k_export_rows(const double* __restrict__ AK, int64_t ldak,
+                              const __nv_bfloat16* __restrict__ AK16, int64_t ldak16,
+                              const double* __restrict__ bK, int64_t row0, int64_t n, int d,
+                              double scale, double* __restrict__ A, double* __restrict__ b) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * (d + 1);
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / (d + 1);
+    const int j = (int)(e % (d + 1));
+    if (j < d) {
+      if (A) {
+        const double v = AK ? AK[(row0 + i) * ldak + j]
+                            : (double)__bfloat162float(AK16[(row0 + i) * ldak16 + j]);
+        A[i * d + j] = v * scale;
+      }
+    } else if (b) {
+      b[i] = bK[row0 + i] * scale;
+    }
+  }
+}
+
+spcg_status launch_export_rows(spcg_ctx* c, int64_t row0, int64_t n, double* A, double* b) {
+  const Sketch& s = c->sk;
+  const bool cs = s.sched.sketch == SPCG_SKETCH_COUNT;
+  const double scale = cs ? 1.0 : 1.0 / sqrt((double)s.n_pad);
+  const int64_t off = s.sched.K > 0 ? s.stage_off[s.sched.K - 1] : 0;
+  k_export_rows<<<512, 256, 0, c->stream>>>(
+      s.mixed ? nullptr : s.AK + off * s.ldak, s.ldak,
+      reinterpret_cast<const __nv_bfloat16*>(s.AK16) + off * s.ldak16, s.ldak16, s.bK + off, row0,
+      n, c->d, scale, A, b);
+  SPCG_CK(cudaGetLastError());
+  return SPCG_OK;
+}
+
+// The FP32 copy of X that the mixed-precision Stage II iterates on.
+__global__ void k_to_f32(const double* __restrict__ X, int64_t ldx, int64_t N, int d,
+                         float* __restrict__ Xf, int64_t ldxf) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / d;
+    const int j = (int)(e % d);
+    Xf[i * ldxf + j] = __double2float_rn(X[i * ldx + j]);
+  }
+}
+
+spcg_status launch_to_f32(spcg_ctx* c) {
+  k_to_f32<<<4 * c->num_sms, 512, 0, c->stream>>>(c->X, c->ldx, c->N, c->d, c->Xf, c->ldxf);
+  SPCG_CK(cudaGetLastError());
+  c->n_launch += 1;
   return SPCG_OK;
 }
 

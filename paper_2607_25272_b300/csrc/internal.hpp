@@ -19,10 +19,15 @@ struct DevScalars {
   double norm_rb;    // last check: ||R beta||
 };
 
-// Geometry of the fused pass over one operand (rows of FP64 values).
+// Element types of a fused-pass operand.
+enum : int { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2 };
+
+// Geometry of the fused pass over one operand.
 struct PassGeom {
   int64_t m;     // rows
   int d;         // columns
+  int dtype;     // DT_*
+  int esize;     // bytes per element
   int nbox;      // TMA boxes across a row
   int boxc;      // columns per box (even)
   int tm;        // rows per tile (box height)
@@ -61,11 +66,14 @@ struct Sketch {
   uint32_t* gather = nullptr;   // P(j) | sign bit
   int32_t* dest = nullptr;      // pi^{-1}(j) if < m_K else -1
   int32_t* hdest = nullptr;     // sigma_hat^{-1}(j) if < r else -1
-  double* work = nullptr;       // N' x ldw transform buffer (multi-pass only)
+  double* work = nullptr;       // N' x ldw int64 transform buffer (multi-pass only)
   int64_t ldw = 0;
   size_t work_bytes = 0;
-  double* AK = nullptr;         // m_K x ldak sketched prefix (pi order)
+  double* AK = nullptr;         // m_K x ldak sketched prefix (pi order), FP64 mode
   int64_t ldak = 0;
+  uint16_t* AK16 = nullptr;     // m_K x ldak16 BF16 prefix, mixed mode
+  int64_t ldak16 = 0;
+  int64_t mK16_alloc = 0;
   double* bK = nullptr;         // m_K
   int64_t mK_alloc = 0;
   double* Ahat = nullptr;       // r x d column-major (ld = r), QR in place
@@ -74,7 +82,12 @@ struct Sketch {
   double* R = nullptr;          // d x d row-major upper
   double* Rinv = nullptr;       // d x d row-major upper
   double* RinvT = nullptr;      // d x d row-major lower (R^{-T})
-  PassGeom geom[SPCG_MAX_STAGES];  // fused-pass geometry of stage i (rows [0, m_i))
+  unsigned long long* colmax = nullptr;  // d + 1: largest |x| per column (bit pattern)
+  int* colshift = nullptr;      // d + 1: fixed-point scale exponent per column
+  PassGeom geom[SPCG_MAX_STAGES];  // fused-pass geometry of stage i
+  int64_t stage_off[SPCG_MAX_STAGES];  // first row of stage i in AK/AK16/bK (SRHT: 0)
+  int64_t rows_alloc = 0;              // rows of AK/AK16/bK
+  bool mixed = false;             // prefix stored as BF16 (SPCG_PREC_MIXED)
 };
 
 }  // namespace spcg
@@ -97,6 +110,12 @@ struct spcg_ctx {
   spcg::Sketch sk;
   spcg::PassGeom gx{};           // pass geometry over X
   bool gx_ready = false;
+  float* Xf = nullptr;           // FP32 copy of X (mixed precision)
+  float* mlp_x = nullptr;        // schedule-model input (4) and two feature scalars
+  float* mlp_y = nullptr;        // schedule-model output (up to 64)
+  double* feat_part = nullptr;   // feature partial sums
+  int64_t ldxf = 0;
+  spcg::PassGeom gxf{};          // pass geometry over Xf
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // launch accounting and optional per-pass event timing
   int64_t n_launch = 0;
@@ -127,10 +146,17 @@ spcg_status from_cuda(cudaError_t e);
 spcg_status launch_sketch_maps(spcg_ctx* c);
 // fwht.cu
 spcg_status launch_transform(spcg_ctx* c);
+spcg_status launch_colscales(spcg_ctx* c);
+// countsketch.cu
+spcg_status launch_countsketch(spcg_ctx* c);
+spcg_status launch_export_rows(spcg_ctx* c, int64_t row0, int64_t n, double* A, double* b);
+spcg_status launch_to_f32(spcg_ctx* c);   // X -> Xf
 // qr.cu
 spcg_status launch_precond_factor(spcg_ctx* c);
 // pcg.cu
 spcg_status make_pass_geom(const double* A, int64_t m, int d, int64_t lda, PassGeom* g);
+spcg_status make_pass_geom_t(const void* A, int64_t m, int d, int64_t lda, int dtype,
+                             PassGeom* g);
 spcg_status pass_resid(spcg_ctx* c, const PassGeom& g, const double* b, const double* x);
 spcg_status pass_gram_iter(spcg_ctx* c, const PassGeom& g, int pp, int gp, int start,
                            int check, double tau);

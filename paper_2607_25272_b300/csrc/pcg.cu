@@ -11,6 +11,8 @@
 //   k_precond   z = R^{-1} u, partial dots g.z and ||R beta||^2
 // The stage start uses the same pass in residual mode: g = A^T (b - A beta).
 // All reductions run in a fixed order, so two runs give identical bits.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -74,9 +76,9 @@ struct PassArgs {
   int64_t m;
   int d, nbox, boxc, tm, ntiles, stages;
   uint32_t tx_bytes;       // bytes one stage's boxes deliver
-  uint32_t slot_doubles;   // doubles between box slots (128-byte multiple)
-  uint32_t stage_doubles;  // doubles between stages
-  uint32_t region_doubles; // doubles of the staging region (also the reduction scratch)
+  uint32_t slot_elems;     // elements between box slots (128-byte multiple)
+  uint32_t stage_elems;    // elements between stages
+  uint32_t region_bytes;   // bytes of the staging region (also the reduction scratch)
   int mode;
   const double* vec;       // PLAIN: p; RESID: beta
   const double* b;         // RESID: right-hand side
@@ -106,16 +108,40 @@ __device__ __forceinline__ double warp_sum_array(const double* v, int n) {
   return warp_allsum(s);
 }
 
-template <int NI>
+// Element types of the operand and the accumulation they use: FP64 rows
+// accumulate in FP64; FP32 rows (the refinement copy of X) in FP32 with
+// compensated products and sums (TwoProd by FMA, TwoSum; Ogita, Rump and
+// Oishi's Dot2), which carries about twice the FP32 precision; BF16 rows (the
+// sketched prefix of Stage I) in plain FP32.
+template <typename T> struct PassElem;
+template <> struct PassElem<double> {
+  using acc = double;
+  static constexpr bool compensated = false;
+  __device__ static double load(double x) { return x; }
+};
+template <> struct PassElem<float> {
+  using acc = float;
+  static constexpr bool compensated = true;
+  __device__ static float load(float x) { return x; }
+};
+template <> struct PassElem<__nv_bfloat16> {
+  using acc = float;
+  static constexpr bool compensated = false;
+  __device__ static float load(__nv_bfloat16 x) { return __bfloat162float(x); }
+};
+
+template <typename T, int NI>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant__ CUtensorMap tmap,
                                                           const PassArgs a) {
+  using E = PassElem<T>;
+  using acc_t = typename E::acc;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base_addr = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((128u - (base_addr & 127u)) & 127u);
-  double* tiles = reinterpret_cast<double*>(smem);
-  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + (size_t)a.region_doubles);
+  T* tiles = reinterpret_cast<T*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.region_bytes);
   uint64_t* empty = full + kMaxStages;
-  double* vec_s = reinterpret_cast<double*>(empty + kMaxStages);  // NI*32 doubles
+  acc_t* vec_s = reinterpret_cast<acc_t*>(empty + kMaxStages);  // NI*32 values
   __shared__ int s_flag;       // 1 = skip the pass (done / error)
   __shared__ int s_abort;
   __shared__ double s_scal[2];
@@ -164,7 +190,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
     for (int j = tid; j < NI * 32; j += blockDim.x) {
       double v = 0.0;
       if (j < a.d) v = a.z[j] + ratio * a.p_prev[j];
-      vec_s[j] = v;
+      vec_s[j] = (acc_t)v;
       if (blockIdx.x == 0 && j < a.d) a.p_next[j] = v;
     }
     if (blockIdx.x == 0 && tid == 0) {
@@ -172,16 +198,16 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
       a.scal->iters += 1;
     }
   } else {
-    for (int j = tid; j < NI * 32; j += blockDim.x) vec_s[j] = (j < a.d) ? a.vec[j] : 0.0;
+    for (int j = tid; j < NI * 32; j += blockDim.x) vec_s[j] = (acc_t)((j < a.d) ? a.vec[j] : 0.0);
   }
   __syncthreads();
 
   const int my_tiles =
       (blockIdx.x < a.ntiles) ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-  double wacc[NI];
+  acc_t wacc[NI], wcmp[NI];
 #pragma unroll
-  for (int i = 0; i < NI; ++i) wacc[i] = 0.0;
+  for (int i = 0; i < NI; ++i) wacc[i] = wcmp[i] = (acc_t)0;
   int issued = 0, skipped = -1;   // producer thread (tid 0) only
 
   if (warp == 0) {
@@ -204,9 +230,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
         }
         const int tile = blockIdx.x + k * gridDim.x;
         mbar_expect_tx(&full[s], a.tx_bytes);
-        double* dst = tiles + (size_t)s * a.stage_doubles;
+        T* dst = tiles + (size_t)s * a.stage_elems;
         for (int bx = 0; bx < a.nbox; ++bx)
-          tma_load_2d(dst + (size_t)bx * a.slot_doubles, &tmap, bx * a.boxc, tile * a.tm,
+          tma_load_2d(dst + (size_t)bx * a.slot_elems, &tmap, bx * a.boxc, tile * a.tm,
                       &full[s]);
       }
     }
@@ -217,7 +243,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
       const int c = lane + 32 * i;
-      off[i] = (c < a.d) ? (c / a.boxc) * (int)a.slot_doubles + (c % a.boxc) : -1;
+      off[i] = (c < a.d) ? (c / a.boxc) * (int)a.slot_elems + (c % a.boxc) : -1;
     }
     for (int k = 0; k < my_tiles; ++k) {
       const int s = k % a.stages;
@@ -228,19 +254,32 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
       }
       const int tile = blockIdx.x + k * gridDim.x;
       const int64_t row0 = (int64_t)tile * a.tm;
-      const double* st = tiles + (size_t)s * a.stage_doubles;
+      const T* st = tiles + (size_t)s * a.stage_elems;
       for (int rr = cw; rr < a.tm; rr += kConsumers) {
         if (row0 + rr >= a.m) break;
-        const double* rowp = st + rr * a.boxc;
-        double t = 0.0;
+        const T* rowp = st + rr * a.boxc;
+        acc_t t = (acc_t)0;
 #pragma unroll
         for (int i = 0; i < NI; ++i)
-          if (off[i] >= 0) t = fma(rowp[off[i]], vec_s[lane + 32 * i], t);
+          if (off[i] >= 0) t = fma(E::load(rowp[off[i]]), vec_s[lane + 32 * i], t);
         t = warp_allsum(t);
-        if (a.mode == PASS_RESID) t = a.b[row0 + rr] - t;
+        if (a.mode == PASS_RESID) t = (acc_t)a.b[row0 + rr] - t;
 #pragma unroll
-        for (int i = 0; i < NI; ++i)
-          if (off[i] >= 0) wacc[i] = fma(t, rowp[off[i]], wacc[i]);
+        for (int i = 0; i < NI; ++i) {
+          if (off[i] < 0) continue;
+          const acc_t x = E::load(rowp[off[i]]);
+          if constexpr (E::compensated) {
+            const acc_t pr = t * x;
+            const acc_t pe = fma(t, x, -pr);          // exact product error
+            const acc_t sm = wacc[i] + pr;
+            const acc_t bb = sm - wacc[i];
+            const acc_t se = (wacc[i] - (sm - bb)) + (pr - bb);   // exact sum error
+            wacc[i] = sm;
+            wcmp[i] += pe + se;
+          } else {
+            wacc[i] = fma(t, x, wacc[i]);
+          }
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
@@ -259,10 +298,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
   __syncthreads();
 
   // ---- CTA partial: fixed-order sum over the consumer warps ----
-  double* red = tiles;   // reuse stage memory: kConsumers x (NI*32)
+  double* red = reinterpret_cast<double*>(smem);   // reuse stage memory: kConsumers x (NI*32)
   if (warp > 0) {
 #pragma unroll
-    for (int i = 0; i < NI; ++i) red[(warp - 1) * NI * 32 + lane + 32 * i] = wacc[i];
+    for (int i = 0; i < NI; ++i)
+      red[(warp - 1) * NI * 32 + lane + 32 * i] = (double)wacc[i] + (double)wcmp[i];
   }
   __syncthreads();
   for (int j = tid; j < a.d; j += blockDim.x) {
@@ -448,17 +488,22 @@ static int ni_for(int d) {
   return ni;
 }
 
-spcg_status make_pass_geom(const double* A, int64_t m, int d, int64_t lda, PassGeom* g) {
-  if (m < 1 || d < 1 || d > SPCG_MAX_D || lda < d || (lda * 8) % 16 != 0 ||
+spcg_status make_pass_geom_t(const void* A, int64_t m, int d, int64_t lda, int dtype,
+                             PassGeom* g) {
+  const int es = dtype == DT_F64 ? 8 : (dtype == DT_F32 ? 4 : 2);
+  if (m < 1 || d < 1 || d > SPCG_MAX_D || lda < d || (lda * es) % 16 != 0 ||
       ((uintptr_t)A & 15u) != 0)
     return SPCG_E_INVALID_ARG;
   g->m = m;
   g->d = d;
+  g->dtype = dtype;
+  g->esize = es;
   g->nbox = (d + 255) / 256;
+  const int align = 16 / es;   // box inner extent: a multiple of 16 bytes
   int bc = (d + g->nbox - 1) / g->nbox;
-  bc = (bc + 1) & ~1;   // box inner extent: a multiple of 16 bytes
+  bc = (bc + align - 1) / align * align;
   g->boxc = bc;
-  const int row_bytes = g->nbox * bc * 8;
+  const int row_bytes = g->nbox * bc * es;
   int tm = 32768 / row_bytes;
   if (tm > 8) tm &= ~7;
   if (tm < 1) tm = 1;
@@ -466,7 +511,7 @@ spcg_status make_pass_geom(const double* A, int64_t m, int d, int64_t lda, PassG
   if (tm > m) tm = (int)m;
   g->tm = tm;
   g->ntiles = (int)((m + tm - 1) / tm);
-  const size_t slot = (((size_t)tm * bc * 8) + 127) & ~(size_t)127;
+  const size_t slot = (((size_t)tm * bc * es) + 127) & ~(size_t)127;
   const size_t stage = slot * g->nbox;
   int stages = (int)((192 * 1024) / stage);
   if (stages > kMaxStages) stages = kMaxStages;
@@ -482,29 +527,49 @@ spcg_status make_pass_geom(const double* A, int64_t m, int d, int64_t lda, PassG
   EncodeTiledFn enc = get_encode();
   if (!enc) return SPCG_E_CUDA;
   cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)m};
-  cuuint64_t strides[1] = {(cuuint64_t)(lda * 8)};
+  cuuint64_t strides[1] = {(cuuint64_t)(lda * es)};
   cuuint32_t box[2] = {(cuuint32_t)bc, (cuuint32_t)tm};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(&g->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)A, dims, strides, box, es,
+  cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType tdt = dtype == DT_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                  : dtype == DT_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUresult r = enc(&g->tmap, tdt, 2, const_cast<void*>(A), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? SPCG_OK : SPCG_E_CUDA;
 }
 
-template <int NI>
+spcg_status make_pass_geom(const double* A, int64_t m, int d, int64_t lda, PassGeom* g) {
+  return make_pass_geom_t(A, m, d, lda, DT_F64, g);
+}
+
+template <typename T, int NI>
 static spcg_status launch_pass_ni(spcg_ctx* c, const PassGeom& g, const PassArgs& a, int grid) {
-  SPCG_CK(cudaFuncSetAttribute(k_pass<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  SPCG_CK(cudaFuncSetAttribute(k_pass<T, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)g.smem_bytes));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1));
   if (e0) SPCG_CK(cudaEventRecord(e0, c->stream));
-  k_pass<NI><<<grid, kPassThreads, g.smem_bytes, c->stream>>>(g.tmap, a);
+  k_pass<T, NI><<<grid, kPassThreads, g.smem_bytes, c->stream>>>(g.tmap, a);
   SPCG_CK(cudaGetLastError());
   if (e1) SPCG_CK(cudaEventRecord(e1, c->stream));
   c->n_launch += 1;
   c->n_pass += 1;
-  c->pass_bytes += (uint64_t)g.m * g.d * 8;
+  c->pass_bytes += (uint64_t)g.m * g.d * g.esize;
   return SPCG_OK;
+}
+
+template <typename T>
+static spcg_status dispatch_ni(spcg_ctx* c, const PassGeom& g, const PassArgs& a, int grid) {
+  switch (ni_for(g.d)) {
+    case 1: return launch_pass_ni<T, 1>(c, g, a, grid);
+    case 2: return launch_pass_ni<T, 2>(c, g, a, grid);
+    case 4: return launch_pass_ni<T, 4>(c, g, a, grid);
+    case 8: return launch_pass_ni<T, 8>(c, g, a, grid);
+    case 16: return launch_pass_ni<T, 16>(c, g, a, grid);
+    case 32: return launch_pass_ni<T, 32>(c, g, a, grid);
+    default: return SPCG_E_INVALID_ARG;
+  }
 }
 
 static spcg_status launch_pass(spcg_ctx* c, const PassGeom& g, PassArgs a) {
@@ -518,25 +583,19 @@ static spcg_status launch_pass(spcg_ctx* c, const PassGeom& g, PassArgs a) {
   a.tm = g.tm;
   a.ntiles = g.ntiles;
   a.stages = g.stages;
-  a.tx_bytes = (uint32_t)((size_t)g.nbox * g.boxc * g.tm * 8);
-  a.slot_doubles = (uint32_t)(g.stage_bytes / g.nbox / 8);
-  a.stage_doubles = (uint32_t)(g.stage_bytes / 8);
-  a.region_doubles = (uint32_t)(g.region_bytes / 8);
+  a.tx_bytes = (uint32_t)((size_t)g.nbox * g.boxc * g.tm * g.esize);
+  a.slot_elems = (uint32_t)(g.stage_bytes / g.nbox / g.esize);
+  a.stage_elems = (uint32_t)(g.stage_bytes / g.esize);
+  a.region_bytes = (uint32_t)g.region_bytes;
   a.partials = c->pb.partials;
   a.ldp = c->pb.ldp;
   a.scal = c->scal;
   a.spin = c->opts.spin_budget > 0 ? c->opts.spin_budget : (1ll << 31);
   a.inject_stall = c->opts.inject_stall;
   c->pb.last_grid = grid;
-  switch (ni_for(g.d)) {
-    case 1: return launch_pass_ni<1>(c, g, a, grid);
-    case 2: return launch_pass_ni<2>(c, g, a, grid);
-    case 4: return launch_pass_ni<4>(c, g, a, grid);
-    case 8: return launch_pass_ni<8>(c, g, a, grid);
-    case 16: return launch_pass_ni<16>(c, g, a, grid);
-    case 32: return launch_pass_ni<32>(c, g, a, grid);
-    default: return SPCG_E_INVALID_ARG;
-  }
+  if (g.dtype == DT_F64) return dispatch_ni<double>(c, g, a, grid);
+  if (g.dtype == DT_F32) return dispatch_ni<float>(c, g, a, grid);
+  return dispatch_ni<__nv_bfloat16>(c, g, a, grid);
 }
 
 spcg_status pass_resid(spcg_ctx* c, const PassGeom& g, const double* b, const double* x) {
@@ -627,9 +686,9 @@ namespace spcg {
 template <int NI>
 static spcg_status launch_gram_scratch_ni(const PassGeom& g, const PassArgs& a, int grid,
                                           cudaStream_t st) {
-  SPCG_CK(cudaFuncSetAttribute(k_pass<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  SPCG_CK(cudaFuncSetAttribute(k_pass<double, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)g.smem_bytes));
-  k_pass<NI><<<grid, kPassThreads, g.smem_bytes, st>>>(g.tmap, a);
+  k_pass<double, NI><<<grid, kPassThreads, g.smem_bytes, st>>>(g.tmap, a);
   SPCG_CK(cudaGetLastError());
   return SPCG_OK;
 }
@@ -648,9 +707,9 @@ spcg_status launch_gram_with_scratch(const PassGeom& g, const double* p, double*
   a.ntiles = g.ntiles;
   a.stages = g.stages;
   a.tx_bytes = (uint32_t)((size_t)g.nbox * g.boxc * g.tm * 8);
-  a.slot_doubles = (uint32_t)(g.stage_bytes / g.nbox / 8);
-  a.stage_doubles = (uint32_t)(g.stage_bytes / 8);
-  a.region_doubles = (uint32_t)(g.region_bytes / 8);
+  a.slot_elems = (uint32_t)(g.stage_bytes / g.nbox / 8);
+  a.stage_elems = (uint32_t)(g.stage_bytes / 8);
+  a.region_bytes = (uint32_t)g.region_bytes;
   a.partials = partials;
   a.ldp = ldp;
   a.scal = scal;
@@ -668,6 +727,82 @@ spcg_status launch_gram_with_scratch(const PassGeom& g, const double* p, double*
   if (s != SPCG_OK) return s;
   k_reduce<<<(g.d + 31) / 32, 256, 0, st>>>(partials, grid, ldp, g.d, w, nullptr, nullptr, scal);
   SPCG_CK(cudaGetLastError());
+  return SPCG_OK;
+}
+
+}  // namespace spcg
+
+namespace spcg {
+
+// Features of the schedule model after stage 1: the condition estimate
+// max R_ii / min R_ii of the preconditioner and the share of b_1 that the
+// stage-1 iterate leaves unexplained, ||b_1 - A_1 beta||^2 / ||b_1||^2 (a
+// noise estimate: sigma^2 (m_1 - d) / ||b_1||^2 at the sketched solution).
+template <typename T>
+__global__ void __launch_bounds__(256) k_feat_resid(const T* __restrict__ A, int64_t lda,
+                                                    const double* __restrict__ b, int64_t m, int d,
+                                                    const double* __restrict__ beta,
+                                                    double* __restrict__ part) {
+  __shared__ double red[2][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double r2 = 0.0, b2 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < m; i += (int64_t)gridDim.x * 8) {
+    double t = 0.0;
+    for (int j = lane; j < d; j += 32) t = fma((double)PassElem<T>::load(A[i * lda + j]), beta[j], t);
+    t = warp_allsum(t);
+    const double r = b[i] - t;
+    r2 = fma(r, r, r2);
+    b2 = fma(b[i], b[i], b2);
+  }
+  if (lane == 0) {
+    red[0][warp] = r2;
+    red[1][warp] = b2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      x += red[0][w];
+      y += red[1][w];
+    }
+    part[2 * blockIdx.x] = x;
+    part[2 * blockIdx.x + 1] = y;
+  }
+}
+
+__global__ void k_feat_final(const double* __restrict__ part, int nb, const double* __restrict__ R,
+                             int d, float* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double x = 0.0, y = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    x += part[2 * i];
+    y += part[2 * i + 1];
+  }
+  double mx = 0.0, mn = INFINITY;
+  for (int i = 0; i < d; ++i) {
+    const double v = fabs(R[(size_t)i * d + i]);
+    mx = fmax(mx, v);
+    mn = fmin(mn, v);
+  }
+  out[0] = (float)log10(mx / mn);
+  out[1] = (float)log10(fmax(x, 1e-300) / fmax(y, 1e-300));
+}
+
+spcg_status launch_features(spcg_ctx* c, const double* beta, float* dev_out2) {
+  const Sketch& s = c->sk;
+  const int64_t m1 = s.sched.m[0];
+  const int nb = 128;
+  if (s.mixed)
+    k_feat_resid<__nv_bfloat16><<<nb, 256, 0, c->stream>>>(
+        reinterpret_cast<const __nv_bfloat16*>(s.AK16), s.ldak16, s.bK, m1, c->d, beta,
+        c->feat_part);
+  else
+    k_feat_resid<double><<<nb, 256, 0, c->stream>>>(s.AK, s.ldak, s.bK, m1, c->d, beta,
+                                                     c->feat_part);
+  SPCG_CK(cudaGetLastError());
+  k_feat_final<<<1, 32, 0, c->stream>>>(c->feat_part, nb, s.R, c->d, dev_out2);
+  SPCG_CK(cudaGetLastError());
+  c->n_launch += 2;
   return SPCG_OK;
 }
 

@@ -9,12 +9,16 @@
 // written during step k, so the CTAs do not race; the diagonal alpha_k is
 // recorded separately.  FP64 throughout: at kappa = 1e8 the sketch must be
 // factored well below 1/kappa relative error.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.hpp"
 
+namespace cg = cooperative_groups;
+
 namespace spcg {
 
-constexpr int QR_WARPS = 4;
+constexpr int QR_WARPS = 8;
 
 // Deterministic block sum (fixed order over warps).
 template <int NW>
@@ -30,16 +34,26 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Step k: s2 = ||x(k+1:r)||^2, alpha = -sign(x_k) ||x||, v = x - alpha e_k;
+// every trailing column j gets a_j -= (2 / v.v) (v.a_j) v.  The reflector
+// column is staged in shared memory when it fits; each warp owns trailing
+// columns and keeps eight independent partial sums so that eight loads per
+// lane are in flight (the step is bound by L2 latency, not arithmetic).
 __global__ void __launch_bounds__(QR_WARPS * 32)
     k_householder_step(double* __restrict__ A, int64_t r, int d, int k,
-                       double* __restrict__ Rdiag) {
+                       double* __restrict__ Rdiag, int staged) {
+  extern __shared__ double vs[];   // x(k : r) when staged
   __shared__ double red[QR_WARPS];
   const double* colk = A + (int64_t)k * r;
-  // sum of squares of x(k+1 : r)
+  const int64_t len = r - k;       // rows k .. r-1
+  if (staged)
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) vs[i] = colk[k + i];
+  __syncthreads();
+  const double* v = staged ? vs : colk + k;   // v[i] = x_{k+i}
   double s2 = 0.0;
-  for (int64_t i = k + 1 + threadIdx.x; i < r; i += blockDim.x) s2 += colk[i] * colk[i];
+  for (int64_t i = 1 + threadIdx.x; i < len; i += blockDim.x) s2 += v[i] * v[i];
   s2 = block_sum<QR_WARPS>(s2, red);
-  const double x0 = colk[k];
+  const double x0 = v[0];
   const double normx = sqrt(x0 * x0 + s2);
   const double alpha = (x0 >= 0.0) ? -normx : normx;
   const double v0 = x0 - alpha;
@@ -48,16 +62,98 @@ __global__ void __launch_bounds__(QR_WARPS * 32)
   if (vv == 0.0) return;
   const double tau = 2.0 / vv;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // trailing columns j = k+1+gw, gw over all warps of the grid
   for (int j = k + 1 + blockIdx.x * QR_WARPS + warp; j < d; j += gridDim.x * QR_WARPS) {
-    double* colj = A + (int64_t)j * r;
-    double s = 0.0;
-    for (int64_t i = k + 1 + lane; i < r; i += 32) s += colk[i] * colj[i];
-    s = warp_allsum(s) + v0 * colj[k];
+    double* cj = A + (int64_t)j * r + k;      // cj[i] = a_{k+i, j}
+    double p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t i = 1 + lane;
+    for (; i + 7 * 32 < len; i += 8 * 32) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) p[u] = fma(v[i + u * 32], cj[i + u * 32], p[u]);
+    }
+    for (; i < len; i += 32) p[0] = fma(v[i], cj[i], p[0]);
+    double s = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+    s = warp_allsum(s) + v0 * cj[0];
     const double f = tau * s;
-    if (lane == 0) colj[k] -= f * v0;
-    for (int64_t i = k + 1 + lane; i < r; i += 32) colj[i] -= f * colk[i];
+    if (lane == 0) cj[0] -= f * v0;
+    for (int64_t i2 = 1 + lane; i2 < len; i2 += 32) cj[i2] = fma(-f, v[i2], cj[i2]);
   }
+}
+
+// Step k with the rows of the trailing matrix split over a cluster of 8 CTAs
+// and its columns dealt round-robin to the clusters of the grid.  Each CTA
+// sums its rows' share of ||x(k+1:r)||^2 and of every dot v.a_j; the shares
+// meet through distributed shared memory and are added in rank order, so the
+// result does not depend on timing.  The cluster barrier is the hardware
+// barrier of the thread-block cluster (no software spin).
+constexpr int QRC = 8;            // CTAs per cluster
+constexpr int QRC_WARPS = 8;
+constexpr int QRC_MAXCOLS = 128;  // trailing columns per cluster per step
+
+__global__ void __cluster_dims__(QRC, 1, 1) __launch_bounds__(QRC_WARPS * 32)
+    k_householder_cluster(double* __restrict__ A, int64_t r, int d, int k,
+                          double* __restrict__ Rdiag) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  const int ncl = gridDim.x / QRC, cl = blockIdx.x / QRC;
+  __shared__ double part_s2;
+  __shared__ double pdot[QRC_MAXCOLS];
+  __shared__ double red[QRC_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double* colk = A + (int64_t)k * r;
+  const int64_t len = r - k;
+  const int64_t chunk = (len + QRC - 1) / QRC;
+  const int64_t lo = q * chunk;                         // rows k+lo .. k+hi-1
+  const int64_t hi = (lo + chunk < len) ? lo + chunk : len;
+  // share of sum x_i^2 over rows k+1..r-1
+  double s2 = 0.0;
+  for (int64_t i = (lo > 1 ? lo : 1) + threadIdx.x; i < hi; i += blockDim.x) {
+    const double x = colk[k + i];
+    s2 = fma(x, x, s2);
+  }
+  s2 = block_sum<QRC_WARPS>(s2, red);
+  if (threadIdx.x == 0) part_s2 = s2;
+  cluster.sync();
+  double tot = 0.0;
+  for (int rr = 0; rr < QRC; ++rr) tot += *cluster.map_shared_rank(&part_s2, rr);
+  const double x0 = colk[k];
+  const double normx = sqrt(x0 * x0 + tot);
+  const double alpha = (x0 >= 0.0) ? -normx : normx;
+  const double v0 = x0 - alpha;
+  const double vv = v0 * v0 + tot;
+  if (blockIdx.x == 0 && threadIdx.x == 0) Rdiag[k] = alpha;
+  const int ncols = d - k - 1;
+  // this cluster's columns: j = k + 1 + cl + c * ncl, c = 0, 1, ...
+  const int mycols = ncols > cl ? (ncols - cl + ncl - 1) / ncl : 0;
+  if (vv != 0.0) {
+    for (int c = warp; c < mycols; c += QRC_WARPS) {
+      const double* cj = A + (int64_t)(k + 1 + cl + c * ncl) * r + k;
+      double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      int64_t i = lo + lane;
+      for (; i + 96 < hi; i += 128) {
+        const double va = (i == 0) ? v0 : colk[k + i];
+        p0 = fma(va, cj[i], p0);
+        p1 = fma(colk[k + i + 32], cj[i + 32], p1);
+        p2 = fma(colk[k + i + 64], cj[i + 64], p2);
+        p3 = fma(colk[k + i + 96], cj[i + 96], p3);
+      }
+      for (; i < hi; i += 32) p0 = fma((i == 0) ? v0 : colk[k + i], cj[i], p0);
+      const double p = warp_allsum((p0 + p1) + (p2 + p3));
+      if (lane == 0) pdot[c] = p;
+    }
+  }
+  cluster.sync();
+  if (vv != 0.0) {
+    const double tau = 2.0 / vv;
+    for (int c = warp; c < mycols; c += QRC_WARPS) {
+      double sj = 0.0;
+      for (int rr = 0; rr < QRC; ++rr) sj += *cluster.map_shared_rank(&pdot[c], rr);
+      const double f = tau * sj;
+      double* cj = A + (int64_t)(k + 1 + cl + c * ncl) * r + k;
+      for (int64_t i = lo + lane; i < hi; i += 32)
+        cj[i] = fma(-f, (i == 0) ? v0 : colk[k + i], cj[i]);
+    }
+  }
+  cluster.sync();   // no CTA leaves while another still reads its shared memory
 }
 
 // R (row-major upper, diag > 0) from the reduced matrix: row i of R is row i
@@ -123,11 +219,27 @@ spcg_status launch_precond_factor(spcg_ctx* c) {
   Sketch& s = c->sk;
   const int d = c->d;
   const int64_t r = s.sched.r;
+  int ncl = c->num_sms / QRC;
+  if (ncl < 1) ncl = 1;
+  const bool use_cluster = ((d - 1 + ncl - 1) / ncl) <= QRC_MAXCOLS;
+  const size_t stage_cap = 200 * 1024;
+  const int staged = (size_t)r * 8 <= stage_cap;
+  if (!use_cluster && staged)
+    SPCG_CK(cudaFuncSetAttribute(k_householder_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)r * 8)));
   for (int k = 0; k < d; ++k) {
     const int cols = d - k - 1;
-    int grid = (cols + QR_WARPS - 1) / QR_WARPS;
-    if (grid < 1) grid = 1;
-    k_householder_step<<<grid, QR_WARPS * 32, 0, c->stream>>>(s.Ahat, r, d, k, s.Rdiag);
+    if (use_cluster) {
+      int g = cols < ncl ? cols : ncl;   // clusters with at least one column
+      if (g < 1) g = 1;
+      k_householder_cluster<<<g * QRC, QRC_WARPS * 32, 0, c->stream>>>(s.Ahat, r, d, k, s.Rdiag);
+    } else {
+      int grid = (cols + QR_WARPS - 1) / QR_WARPS;
+      if (grid < 1) grid = 1;
+      const size_t smem = staged ? (size_t)(r - k) * 8 : 0;
+      k_householder_step<<<grid, QR_WARPS * 32, smem, c->stream>>>(s.Ahat, r, d, k, s.Rdiag,
+                                                                   staged);
+    }
   }
   c->n_launch += d + 3;
   SPCG_CK(cudaGetLastError());

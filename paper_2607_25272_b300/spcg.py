@@ -40,6 +40,10 @@ SPCG_E_TIMEOUT = 6
 SPCG_E_STATE = 7
 
 PREC_FP64 = 0
+PREC_MIXED = 1
+SKETCH_SRHT = 0
+SKETCH_COUNT = 1
+DTYPE_CODE = {"float64": 0, "float32": 1, "bfloat16": 2}
 
 
 class SpcgError(RuntimeError):
@@ -57,11 +61,13 @@ class Schedule(ctypes.Structure):
         ("tol", ctypes.c_double),
         ("max_iters", ctypes.c_int32),
         ("max_restarts", ctypes.c_int32),
+        ("sketch", ctypes.c_int32),
     ]
 
     def as_dict(self):
         return {"m": list(self.m[: self.K]), "a": list(self.a[: self.K]), "r": self.r,
-                "tol": self.tol, "max_iters": self.max_iters, "max_restarts": self.max_restarts}
+                "tol": self.tol, "max_iters": self.max_iters, "max_restarts": self.max_restarts,
+                "sketch": self.sketch}
 
 
 class Opts(ctypes.Structure):
@@ -94,12 +100,24 @@ class Info(ctypes.Structure):
     ]
 
 
+class ProblemF32(ctypes.Structure):
+    _fields_ = [
+        ("X", ctypes.c_void_p),
+        ("Y", ctypes.c_void_p),
+        ("N", ctypes.c_int64),
+        ("d", ctypes.c_int32),
+        ("ldx", ctypes.c_int64),
+        ("beta", ctypes.c_void_p),
+    ]
+
+
 _lib = None
 
 _P = ctypes.c_void_p
 _SIGS = {
     "spcg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "spcg_default_schedule": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Schedule)]),
+    "spcg_tuned_schedule": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Schedule)]),
     "spcg_create": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P,
                                    ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "spcg_destroy": (None, [_P]),
@@ -116,6 +134,34 @@ _SIGS = {
     "spcg_export_sketch": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
     "spcg_export_precond": (ctypes.c_int, [_P, _P, _P, _P]),
     "spcg_gram_apply": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "spcg_gram_apply_typed": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                             _P, _P]),
+    "spcg_batch_create": (ctypes.c_int, [ctypes.POINTER(ProblemF32), ctypes.c_int32, _P,
+                                         ctypes.POINTER(_P)]),
+    "spcg_batch_destroy": (None, [_P]),
+    "spcg_batch_solve": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "spcg_batch_set_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "spcg_batch_autotune": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    "spcg_num_candidates": (ctypes.c_int32, []),
+    "spcg_candidate_schedule": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(Schedule)]),
+    "spcg_features": (ctypes.c_int, [_P, _P, _P]),
+    "spcg_solve_learned": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_int32, _P,
+                                          ctypes.c_double, _P, ctypes.POINTER(Info),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "spcg_solve_candidate": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
+                                            ctypes.c_int32, _P, ctypes.POINTER(Info)]),
+    "spcg_mlp_params": (ctypes.c_int64, [ctypes.c_int32]),
+    "spcg_mlp_workspace_floats": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int64]),
+    "spcg_mlp_forward": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P]),
+    "spcg_mlp_grad": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P, _P, _P]),
+    "spcg_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_float,
+                                     ctypes.c_int32, _P, _P]),
+    "spcg_mlp_to_bf16": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
     "spcg_gram_apply_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                                _P, _P, _P]),
 }
@@ -174,8 +220,15 @@ def spcg_default_schedule(N, d):
     return s
 
 
-def make_schedule(m, a, r, tol=1e-6, max_iters=100, max_restarts=5):
+def spcg_tuned_schedule(N, d):
     s = Schedule()
+    _check(lib().spcg_tuned_schedule(N, d, ctypes.byref(s)), "spcg_tuned_schedule")
+    return s
+
+
+def make_schedule(m, a, r, tol=1e-6, max_iters=100, max_restarts=5, sketch=0):
+    s = Schedule()
+    s.sketch = int(sketch)
     s.K = len(m)
     for i, (mi, ai) in enumerate(zip(m, a)):
         s.m[i] = int(mi)
@@ -267,6 +320,38 @@ class Solver:
             _check(st, "spcg_solve")
         return beta, info, st
 
+    def features(self, beta):
+        out = (ctypes.c_float * 4)()
+        _check(lib().spcg_features(self.ctx, _ptr(beta), out), "spcg_features")
+        return list(out)
+
+    def solve_learned(self, seed, Wb, norm, tol=1e-6, beta=None, raise_on_error=True):
+        """Algorithm 1 with the model's schedule (Wb None: the paper's schedule)."""
+        import torch
+        if beta is None:
+            beta = torch.empty(self.d, dtype=torch.float64, device=self.X.device)
+        info = Info()
+        choice = ctypes.c_int32(-1)
+        normc = (ctypes.c_float * 8)(*[float(v) for v in norm]) if norm is not None else None
+        st = lib().spcg_solve_learned(self.ctx, seed, _ptr(Wb) if Wb is not None else None, 25,
+                                      normc, tol, _ptr(beta), ctypes.byref(info),
+                                      ctypes.byref(choice))
+        if raise_on_error:
+            _check(st, "spcg_solve_learned")
+        return beta, info, choice.value, st
+
+    def solve_candidate(self, seed, idx, tol=1e-6, reuse_sketch=False, beta=None,
+                        raise_on_error=True):
+        import torch
+        if beta is None:
+            beta = torch.empty(self.d, dtype=torch.float64, device=self.X.device)
+        info = Info()
+        st = lib().spcg_solve_candidate(self.ctx, seed, idx, tol, int(reuse_sketch), _ptr(beta),
+                                        ctypes.byref(info))
+        if raise_on_error:
+            _check(st, "spcg_solve_candidate")
+        return beta, info, st
+
     def export_sketch(self, row0, nrows):
         import torch
         A = torch.empty((max(nrows, 1), self.d), dtype=torch.float64, device=self.X.device)
@@ -287,6 +372,19 @@ class Solver:
                "spcg_export_precond")
         return R, Rinv, Ahat
 
+    def gram_apply_typed(self, A, p, w=None):
+        """w = A^T (A p) for an FP64, FP32 or BF16 operand A (row-major CUDA tensor)."""
+        import torch
+        if w is None:
+            w = torch.empty(self.d, dtype=torch.float64, device=p.device)
+        code = DTYPE_CODE[str(A.dtype).replace("torch.", "")]
+        m = A.shape[0]
+        lda = A.stride(0) if m > 0 else self.d
+        st = lib().spcg_gram_apply_typed(self.ctx, _ptr(A) if m > 0 else None, code, m, lda,
+                                         _ptr(p), _ptr(w))
+        _check(st, "spcg_gram_apply_typed")
+        return w
+
     def gram_apply(self, A, p, w=None):
         import torch
         if w is None:
@@ -296,6 +394,43 @@ class Solver:
         st = lib().spcg_gram_apply(self.ctx, _ptr(A) if m > 0 else None, m, lda, _ptr(p), _ptr(w))
         _check(st, "spcg_gram_apply")
         return w
+
+
+def spcg_candidate_schedule(N, d, idx):
+    s = Schedule()
+    _check(lib().spcg_candidate_schedule(N, d, idx, ctypes.byref(s)), "spcg_candidate_schedule")
+    return s
+
+
+def spcg_mlp_params(n_out):
+    return int(lib().spcg_mlp_params(n_out))
+
+
+def spcg_mlp_forward(Wb, n_out, x, y=None, stream=None):
+    """y = MLP(x); Wb: CUDA int16/uint16 tensor of BF16 bits, x: (B, 4) float32."""
+    import torch
+    B = x.shape[0]
+    if y is None:
+        y = torch.empty((B, n_out), dtype=torch.float32, device=x.device)
+    _check(lib().spcg_mlp_forward(_ptr(Wb), n_out, _ptr(x), B, _ptr(y), _stream_ptr(stream)),
+           "spcg_mlp_forward")
+    return y
+
+
+def spcg_mlp_grad(Wb, n_out, x, t, grad, loss, workspace, stream=None):
+    _check(lib().spcg_mlp_grad(_ptr(Wb), n_out, _ptr(x), _ptr(t), x.shape[0], _ptr(grad),
+                               _ptr(loss), _ptr(workspace), _stream_ptr(stream)), "spcg_mlp_grad")
+
+
+def spcg_mlp_adam(theta, grad, m, v, lr, step, Wb, stream=None):
+    _check(lib().spcg_mlp_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), theta.numel(),
+                               ctypes.c_float(lr), step, _ptr(Wb), _stream_ptr(stream)),
+           "spcg_mlp_adam")
+
+
+def spcg_mlp_to_bf16(theta, Wb, stream=None):
+    _check(lib().spcg_mlp_to_bf16(_ptr(theta), theta.numel(), _ptr(Wb), _stream_ptr(stream)),
+           "spcg_mlp_to_bf16")
 
 
 def spcg_gram_apply_noalloc(A, p, w=None, stream=None):
@@ -327,3 +462,57 @@ def spcg_solve_host(X_host, Y_host, seed, sched=None, opts=None):
         return beta.cpu(), info, st
     finally:
         s.close()
+
+
+class Batch:
+    """Owner of an spcg_batch over lists of FP32 CUDA tensors X_i (N_i x d_i), Y_i."""
+
+    def __init__(self, Xs, Ys, stream=None):
+        import torch
+        self.Xs, self.Ys = list(Xs), list(Ys)
+        self.n = len(self.Xs)
+        self.betas = [torch.zeros(X.shape[1], dtype=torch.float64, device=X.device)
+                      for X in self.Xs]
+        arr = (ProblemF32 * self.n)()
+        for i, (X, Y, b) in enumerate(zip(self.Xs, self.Ys, self.betas)):
+            if X.dtype != torch.float32 or Y.dtype != torch.float32 or X.stride(1) != 1:
+                raise ValueError("batched problems take row-major float32 X and float32 Y")
+            arr[i].X = X.data_ptr()
+            arr[i].Y = Y.data_ptr()
+            arr[i].N = X.shape[0]
+            arr[i].d = X.shape[1]
+            arr[i].ldx = X.stride(0)
+            arr[i].beta = b.data_ptr()
+        h = ctypes.c_void_p()
+        _check(lib().spcg_batch_create(arr, self.n, _stream_ptr(stream), ctypes.byref(h)),
+               "spcg_batch_create")
+        self.h = h
+
+    def solve(self, seed, tol=1e-6, raise_on_error=False):
+        st = (ctypes.c_int32 * self.n)()
+        it = (ctypes.c_int32 * self.n)()
+        ms = ctypes.c_double(0.0)
+        rc = lib().spcg_batch_solve(self.h, seed, tol, st, it, ctypes.byref(ms))
+        if raise_on_error:
+            _check(rc, "spcg_batch_solve")
+        return rc, list(st), list(it), ms.value
+
+    def autotune(self, seed, tol=1e-6):
+        ch = (ctypes.c_int32 * 4)()
+        _check(lib().spcg_batch_autotune(self.h, seed, tol, ch), "spcg_batch_autotune")
+        return list(ch)
+
+    def set_tiles(self, chunk_bytes4):
+        arr = (ctypes.c_int32 * 4)(*chunk_bytes4)
+        _check(lib().spcg_batch_set_tiles(self.h, arr), "spcg_batch_set_tiles")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().spcg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -35,6 +35,14 @@ def test_default_schedule_matches_oracle_reading(N, d):
     assert s.tol == 1e-6 and s.max_iters == 100
 
 
+@pytest.mark.parametrize("N,d", [(1 << 22, 64), (1 << 20, 500), (20000, 50), (1 << 23, 256)])
+def test_tuned_schedule_matches_oracle_reading(N, d):
+    from oracle.spcg import tuned_schedule
+    s = S.spcg_tuned_schedule(N, d)
+    o = tuned_schedule(N, d)
+    assert list(s.m[: s.K]) == o["m"] and list(s.a[: s.K]) == o["a"] and s.r == o["r"]
+
+
 def test_invalid_arguments_rejected_before_any_cuda_call():
     L = S.lib()
     out = ctypes.c_void_p()
@@ -59,5 +67,5 @@ def test_invalid_arguments_rejected_before_any_cuda_call():
 
 def test_struct_layouts_match_header_sizes():
     # spcg_schedule: int32 K, int64 m[40], int32 a[40], int64 r, double tol, 2 x int32
-    assert ctypes.sizeof(S.Schedule) == 8 + 8 * 40 + 4 * 40 + 8 + 8 + 8
+    assert ctypes.sizeof(S.Schedule) == 8 + 8 * 40 + 4 * 40 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(S.Opts) == 4 + 4 + 8 + 16

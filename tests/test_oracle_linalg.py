@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle.linalg import apply_precond, householder_qr, ols, r_factor
+from oracle.linalg import apply_precond, householder_qr, ols, ols_lowmem, r_factor
 from paper_2607_25272_b300.inputs import gaussian_problem, svd_problem
 
 U64 = np.finfo(np.float64).eps / 2
@@ -86,3 +86,9 @@ def test_apply_precond_is_inverse_gram():
     g = rng.standard_normal(9)
     z = apply_precond(R, g)
     assert np.allclose((A.T @ A) @ z, g, atol=1e-12 * np.linalg.norm(g) * np.linalg.cond(A) ** 2)
+
+
+def test_ols_lowmem_matches_ols():
+    X, Y, _ = svd_problem(3000, 30, 1e5, 0.3, seed=13)
+    b1, b2 = ols(X, Y), ols_lowmem(X, Y)
+    assert np.linalg.norm(X @ (b1 - b2)) <= 1e-11 * np.linalg.norm(X @ b1)
