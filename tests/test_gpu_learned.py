@@ -1,0 +1,131 @@
+"""The learned schedule: the MLP kernels against the FP64 oracle MLP, training
+through the library's kernels, and solves with the model's choice.
+
+Tolerances: the GPU network computes in FP32 with BF16 weights; each of its
+three layers sums at most 65 products, so |dy| <= 3 gamma32_65 |y|_abs where
+|y|_abs is the output of the same network run on |x| and |W| (a magnitude
+bound).  Gradients add at most 16 samples per block in FP32 and then the
+blocks in order: |dg| <= gamma32_{B 64 + 64} g_abs with g_abs the largest
+gradient magnitude of the batch (bounded here by max |g|).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import linalg as OL
+from oracle import mlp as OM
+from oracle.metrics import rel_pred_error
+from paper_2607_25272_b300 import schedule_model as SM
+from paper_2607_25272_b300 import spcg as S
+from paper_2607_25272_b300.inputs import paper_problem, svd_problem
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+def g32(n):
+    return n * U32 / (1 - n * U32)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    S.lib()
+
+
+def _weights(n_out, seed):
+    rng = np.random.default_rng(seed)
+    theta = (rng.standard_normal(OM.n_params(n_out)) * 0.3).astype(np.float32)
+    thb = OM.bf16_round(theta)                         # the deployed BF16 weights, as FP64
+    Wb = torch.from_numpy(theta).cuda()
+    bits = torch.zeros(theta.size, dtype=torch.int16, device="cuda")
+    S.spcg_mlp_to_bf16(Wb, bits)
+    return thb, bits
+
+
+@pytest.mark.parametrize("n_out,B", [(25, 1), (25, 37), (7, 200), (64, 16)])
+def test_forward_matches_oracle(n_out, B):
+    thb, bits = _weights(n_out, n_out + B)
+    x = np.random.default_rng(B).standard_normal((B, 4)).astype(np.float32)
+    y = S.spcg_mlp_forward(bits, n_out, torch.from_numpy(x).cuda()).cpu().numpy()
+    ref, _ = OM.forward(thb, x.astype(np.float64), n_out)
+    mag, _ = OM.forward(np.abs(thb), np.abs(x.astype(np.float64)), n_out)
+    assert np.all(np.abs(y - ref) <= 3 * g32(65) * mag + 1e-30)
+
+
+@pytest.mark.parametrize("n_out,B", [(25, 5), (25, 300), (3, 64)])
+def test_gradient_matches_oracle(n_out, B):
+    thb, bits = _weights(n_out, 7 * B + n_out)
+    rng = np.random.default_rng(B)
+    x = rng.standard_normal((B, 4)).astype(np.float32)
+    t = rng.standard_normal((B, n_out)).astype(np.float32)
+    P = S.spcg_mlp_params(n_out)
+    grad = torch.zeros(P, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ws = torch.zeros(int(S.lib().spcg_mlp_workspace_floats(n_out, B)), dtype=torch.float32,
+                     device="cuda")
+    S.spcg_mlp_grad(bits, n_out, torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), grad,
+                    loss, ws)
+    l_ref, g_ref = OM.loss_and_grad(thb, x.astype(np.float64), t.astype(np.float64), n_out)
+    g = grad.cpu().numpy()
+    assert np.all(np.abs(g - g_ref) <= 10 * g32(B * 64 + 64) * np.abs(g_ref).max() + 1e-30)
+    assert abs(loss.item() - l_ref) <= 10 * g32(B * n_out) * l_ref
+
+
+def test_training_kernels_fit_a_smooth_target():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((512, 4))
+    t = np.stack([np.sin(x[:, 0]) + x[:, 1] * x[:, 2], np.abs(x[:, 3]) - 0.5 * x[:, 0]], axis=1)
+    tr = SM.Trainer(n_out=2, seed=1)
+    hist = tr.fit(x, t, steps=800, lr=3e-3)
+    assert hist[-1][1] < 0.1 * hist[0][1]
+
+
+def test_learned_solve_fallback_and_any_choice_converge():
+    X, Y, _ = svd_problem(1 << 16, 64, 1e4, 0.1, seed=3)
+    bh = OL.ols(X, Y)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    s = S.Solver(Xd, Yd)
+    beta, info, choice, st = s.solve_learned(5, None, None, tol=1e-6)
+    assert st == S.SPCG_OK and choice == SM.PAPER_CANDIDATE
+    assert rel_pred_error(X, beta.cpu().numpy(), bh) <= 1e-6
+    # the paper's candidate reproduces the paper's schedule
+    sc = S.spcg_candidate_schedule(1 << 16, 64, SM.PAPER_CANDIDATE)
+    ds = S.spcg_default_schedule(1 << 16, 64)
+    assert list(sc.m[: sc.K]) == list(ds.m[: ds.K]) and list(sc.a[: sc.K]) == list(ds.a[: ds.K])
+    for idx in (0, 1, 12, 24):
+        b2, info2, st2 = s.solve_candidate(5, idx, 1e-6)
+        assert st2 == S.SPCG_OK and rel_pred_error(X, b2.cpu().numpy(), bh) <= 1e-6
+    _, bits = _weights(25, 11)
+    b3, _, ch3, st3 = s.solve_learned(5, bits, [0, 0, 0, 0, 1, 1, 1, 1], tol=1e-6)
+    assert st3 == S.SPCG_OK and 0 <= ch3 < 25
+    assert rel_pred_error(X, b3.cpu().numpy(), bh) <= 1e-6
+    s.close()
+
+
+def test_trained_model_beats_the_paper_schedule_on_held_out_problems():
+    """What the trained network gains over the method without it: on problems
+    drawn like the training set (new seeds), the device time of stages +
+    Stage II with the model's choice against the paper's schedule, both solved
+    to the same tolerance from the same sketch."""
+    Wb, norm = SM.load()
+    if Wb is None:
+        pytest.skip("no trained weights")
+    rng = np.random.default_rng(424242)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(424242)
+    learned, paper = 0.0, 0.0
+    for i in range(16):
+        X, Y, _ = SM.sample_problem(rng, gen, "cuda")
+        s = S.Solver(X, Y)
+        beta, info, choice, st = s.solve_learned(1000 + i, Wb, norm, tol=1e-6)
+        assert st == S.SPCG_OK
+        _, il, stl = s.solve_candidate(1000 + i, choice, 1e-6, reuse_sketch=True)
+        _, ip, stp = s.solve_candidate(1000 + i, SM.PAPER_CANDIDATE, 1e-6, reuse_sketch=True)
+        assert stl == S.SPCG_OK and stp == S.SPCG_OK
+        learned += il.ms_stages + il.ms_refine
+        paper += ip.ms_stages + ip.ms_refine
+        s.close()
+    assert learned < paper
