@@ -57,11 +57,13 @@ enum {
   SPCG_PREC_FP64 = 0,       /* plain FP64 everywhere (the comparator path)    */
   SPCG_PREC_MIXED = 1       /* Stage I reads a BF16 copy of the sketched rows
                                with FP32 accumulation; Stage II iterates on an
-                               FP32 copy of X with compensated (TwoProd/TwoSum)
+                               FP32 copy Xh of X with compensated (TwoProd/TwoSum)
                                accumulation, and every true gradient
                                X^T (Y - X beta) that the stopping rule trusts is
-                               an FP64 pass over X; the sketch, the QR giving R,
-                               R^{-1} and the CG scalars stay FP64            */
+                               computed in double-FP32 arithmetic from the split
+                               X = Xh + Xl (|X - Xh - Xl| <= 2^-48 |X|); the
+                               sketch, the QR giving R, R^{-1} and the CG scalars
+                               stay FP64                                       */
 };
 
 /*

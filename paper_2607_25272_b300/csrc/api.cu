@@ -101,9 +101,11 @@ static spcg_status sync_scalars(spcg_ctx* c) {
 }
 
 // g = A^T (b - A beta), u = R^{-T} g, z = R^{-1} u, dots: the PCG start.
+// df: the gradient comes from the double-FP32 pass over the split of X.
 static spcg_status start_sequence(spcg_ctx* c, const PassGeom& g, const double* b,
-                                  double* beta, int& cur) {
-  SPCG_TRY(pass_resid(c, g, b, beta));
+                                  double* beta, int& cur, bool df = false) {
+  if (df) SPCG_TRY(pass_resid_df(c, c->gxdf, c->tml, b, beta));
+  else SPCG_TRY(pass_resid(c, g, b, beta));
   SPCG_TRY(launch_reduce(c, c->pb.g[cur], nullptr));
   SPCG_TRY(launch_precond_T(c, 0, cur, 0, 0, beta));
   cur ^= 1;
@@ -162,7 +164,7 @@ static spcg_status run_refine(spcg_ctx* c, double tol, int max_iters, int max_re
   for (;;) {
     // true gradient and the stopping test on it
     int cur = 0, pp = 0, gp = 0;
-    SPCG_TRY(start_sequence(c, g, c->Y, beta, cur));
+    SPCG_TRY(start_sequence(c, g, c->Y, beta, cur, c->opts.precision == SPCG_PREC_MIXED));
     SPCG_TRY(launch_check(c, tau));
     SPCG_TRY(sync_scalars(c));
     if (c->host_scal.done) {
@@ -347,9 +349,13 @@ extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, 
   if (c->opts.precision == SPCG_PREC_MIXED) {
     c->ldxf = (d + 3) & ~int64_t(3);
     if ((st = dalloc(&c->Xf, (size_t)N * c->ldxf)) != SPCG_OK) return fail(st);
-    if (c->ldxf > d && cudaMemsetAsync(c->Xf, 0, (size_t)N * c->ldxf * 4, c->stream) != cudaSuccess)
+    if ((st = dalloc(&c->Xl, (size_t)N * c->ldxf)) != SPCG_OK) return fail(st);
+    if (c->ldxf > d && (cudaMemsetAsync(c->Xf, 0, (size_t)N * c->ldxf * 4, c->stream) != cudaSuccess ||
+                        cudaMemsetAsync(c->Xl, 0, (size_t)N * c->ldxf * 4, c->stream) != cudaSuccess))
       return fail(SPCG_E_CUDA);
     if ((st = make_pass_geom_t(c->Xf, N, d, c->ldxf, DT_F32, &c->gxf)) != SPCG_OK) return fail(st);
+    if ((st = make_pass_geom_df(c->Xf, c->Xl, N, d, c->ldxf, &c->gxdf, &c->tml)) != SPCG_OK)
+      return fail(st);
   }
   for (auto& e : c->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(SPCG_E_CUDA);
@@ -388,6 +394,7 @@ extern "C" void spcg_destroy(spcg_ctx* c) {
   dfree(c->scal);
   dfree(c->X_own);
   dfree(c->Xf);
+  dfree(c->Xl);
   dfree(c->sk.AK16);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);

@@ -77,15 +77,25 @@ __global__ void __launch_bounds__(256) k_colmax(const double* __restrict__ X, in
                                                 const double* __restrict__ Y, int64_t N, int d,
                                                 unsigned long long* __restrict__ colmax) {
   const int C = d + 1;
+  const int64_t G = gridDim.x;
   for (int c0 = 0; c0 < C; c0 += blockDim.x) {
     const int c = c0 + threadIdx.x;
     unsigned long long mx = 0;
     if (c < C) {
-      for (int64_t i = blockIdx.x; i < N; i += gridDim.x) {
-        const double v = (c < d) ? X[i * ldx + c] : Y[i];
-        const unsigned long long b =
-            (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-        mx = b > mx ? b : mx;
+      // four rows in flight per thread
+      for (int64_t i = blockIdx.x; i < N; i += 4 * G) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t row = i + u * G;
+          v[u] = (row < N) ? ((c < d) ? X[row * ldx + c] : Y[row]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned long long b =
+              (unsigned long long)__double_as_longlong(v[u]) & 0x7FFFFFFFFFFFFFFFull;
+          mx = b > mx ? b : mx;
+        }
       }
       atomicMax(colmax + c, mx);
     }
@@ -174,29 +184,43 @@ __device__ __forceinline__ void do_round(const FwhtArgs& a, long long* tile, con
     const int t0 = (gi & (h - 1)) | ((gi >> lev) << (lev + G));
     const int col = c0 + c;
     long long v[GN];
+    if (from_global) {
+      // All GN loads are issued before any is used: addresses are clamped to
+      // valid memory and the values masked afterwards, so no load waits
+      // behind a branch.
+      const bool colok = col < a.C;
+      const int colc = colok ? col : 0;
+      if (a.first) {
+        double raw[GN];
+        uint32_t gm[GN];
 #pragma unroll
-    for (int k = 0; k < GN; ++k) {
-      const int t = t0 + k * h;
-      long long x = 0;
-      if (from_global) {
-        if (col < a.C) {
-          if (a.first) {
-            const uint32_t gm = (uint32_t)gmap[t];
-            const int64_t src = (int64_t)(gm & 0x7FFFFFFFu);
-            if (src < a.N) {
-              const double xv = (col < a.d) ? a.X[src * a.ldx + col] : a.Y[src];
-              x = to_fixed(xv, sh[c]);
-              if (gm & 0x80000000u) x = -x;
-            }
-          } else {
-            const int64_t j = low | ((int64_t)t << a.shift_lo) | (high << (a.shift_lo + LOGL));
-            x = a.W[j * a.ldw + col];
-          }
+        for (int k = 0; k < GN; ++k) {
+          gm[k] = (uint32_t)gmap[t0 + k * h];
+          const int64_t src = (int64_t)(gm[k] & 0x7FFFFFFFu);
+          const int64_t srcc = src < a.N ? src : 0;
+          const double* ptr = (colc < a.d) ? a.X + srcc * a.ldx + colc : a.Y + srcc;
+          raw[k] = __ldg(ptr);
+        }
+#pragma unroll
+        for (int k = 0; k < GN; ++k) {
+          const int64_t src = (int64_t)(gm[k] & 0x7FFFFFFFu);
+          long long x = (colok && src < a.N) ? to_fixed(raw[k], sh[c]) : 0;
+          v[k] = (gm[k] & 0x80000000u) ? -x : x;
         }
       } else {
-        x = tile[t * TC + c];
+#pragma unroll
+        for (int k = 0; k < GN; ++k) {
+          const int t = t0 + k * h;
+          const int64_t j = low | ((int64_t)t << a.shift_lo) | (high << (a.shift_lo + LOGL));
+          v[k] = a.W[j * a.ldw + colc];
+        }
+        if (!colok)
+#pragma unroll
+          for (int k = 0; k < GN; ++k) v[k] = 0;
       }
-      v[k] = x;
+    } else {
+#pragma unroll
+      for (int k = 0; k < GN; ++k) v[k] = tile[(t0 + k * h) * TC + c];
     }
     bfly<G>(v);
 #pragma unroll
@@ -320,7 +344,7 @@ spcg_status launch_colscales(spcg_ctx* c) {
   const int C = c->d + 1;
   SPCG_CK(cudaMemsetAsync(s.colmax, 0, (size_t)C * sizeof(unsigned long long), c->stream));
   int cg = (int)((c->N + 63) / 64);
-  if (cg > 4 * c->num_sms) cg = 4 * c->num_sms;
+  if (cg > 8 * c->num_sms) cg = 8 * c->num_sms;
   if (cg < 1) cg = 1;
   k_colmax<<<cg, 256, 0, c->stream>>>(c->X, c->ldx, c->Y, c->N, c->d, s.colmax);
   SPCG_CK(cudaGetLastError());
@@ -404,19 +428,24 @@ spcg_status launch_export_rows(spcg_ctx* c, int64_t row0, int64_t n, double* A, 
   return SPCG_OK;
 }
 
-// The FP32 copy of X that the mixed-precision Stage II iterates on.
+// The FP32 split X = Xh + Xl of the mixed-precision Stage II: the iterations
+// read Xh, the true gradients read both halves.
 __global__ void k_to_f32(const double* __restrict__ X, int64_t ldx, int64_t N, int d,
-                         float* __restrict__ Xf, int64_t ldxf) {
+                         float* __restrict__ Xf, float* __restrict__ Xl, int64_t ldxf) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * d;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / d;
     const int j = (int)(e % d);
-    Xf[i * ldxf + j] = __double2float_rn(X[i * ldx + j]);
+    const double x = X[i * ldx + j];
+    const float h = __double2float_rn(x);
+    Xf[i * ldxf + j] = h;
+    Xl[i * ldxf + j] = __double2float_rn(x - (double)h);
   }
 }
 
 spcg_status launch_to_f32(spcg_ctx* c) {
-  k_to_f32<<<4 * c->num_sms, 512, 0, c->stream>>>(c->X, c->ldx, c->N, c->d, c->Xf, c->ldxf);
+  k_to_f32<<<4 * c->num_sms, 512, 0, c->stream>>>(c->X, c->ldx, c->N, c->d, c->Xf, c->Xl,
+                                                   c->ldxf);
   SPCG_CK(cudaGetLastError());
   c->n_launch += 1;
   return SPCG_OK;

@@ -110,7 +110,10 @@ struct spcg_ctx {
   spcg::Sketch sk;
   spcg::PassGeom gx{};           // pass geometry over X
   bool gx_ready = false;
-  float* Xf = nullptr;           // FP32 copy of X (mixed precision)
+  float* Xf = nullptr;           // FP32 copy of X (mixed precision): Xh = fl32(X)
+  float* Xl = nullptr;           // FP32 remainder: Xl = fl32(X - Xh)
+  spcg::PassGeom gxdf{};         // pass geometry over the pair (Xh, Xl)
+  CUtensorMap tml{};             // tensor map of Xl for that pass
   float* mlp_x = nullptr;        // schedule-model input (4) and two feature scalars
   float* mlp_y = nullptr;        // schedule-model output (up to 64)
   double* feat_part = nullptr;   // feature partial sums
@@ -168,5 +171,9 @@ spcg_status launch_reset_flags(spcg_ctx* c);
 spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1);
 spcg_status prof_collect(spcg_ctx* c);   // after a stream sync
 spcg_status pass_gram_plain(spcg_ctx* c, const PassGeom& g, const double* p);
+spcg_status make_pass_geom_df(const float* Xh, const float* Xl, int64_t m, int d, int64_t lda,
+                              PassGeom* g, CUtensorMap* tml);
+spcg_status pass_resid_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml,
+                          const double* b, const double* x);
 
 }  // namespace spcg

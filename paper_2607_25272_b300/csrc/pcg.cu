@@ -66,8 +66,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-constexpr int kConsumers = 8;                 // consumer warps of k_pass
-constexpr int kPassThreads = 32 * (kConsumers + 1);
+constexpr int kConsumers = 12;                // consumer warps of k_pass (upper bound)
+// Consumer warps per CTA: fewer for the widest rows, whose accumulators need
+// the registers.
+template <int NI>
+struct PassCfg {
+  static constexpr int C = NI >= 32 ? 8 : kConsumers;
+  static constexpr int THREADS = 32 * (C + 1);
+};
 constexpr int kMaxStages = 8;
 
 enum PassMode : int { PASS_PLAIN = 0, PASS_ITER = 1, PASS_RESID = 2 };
@@ -118,22 +124,49 @@ template <> struct PassElem<double> {
   using acc = double;
   static constexpr bool compensated = false;
   __device__ static double load(double x) { return x; }
+  __device__ static void load_vec(const double* p, double (&x)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+  }
 };
 template <> struct PassElem<float> {
   using acc = float;
   static constexpr bool compensated = true;
   __device__ static float load(float x) { return x; }
+  __device__ static void load_vec(const float* p, float (&x)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+  }
 };
 template <> struct PassElem<__nv_bfloat16> {
   using acc = float;
   static constexpr bool compensated = false;
   __device__ static float load(__nv_bfloat16 x) { return __bfloat162float(x); }
+  __device__ static void load_vec(const __nv_bfloat16* p, float (&x)[8]) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {   // a BF16 is the top half of an FP32
+      x[2 * i] = __uint_as_float(w[i] << 16);
+      x[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+  }
 };
 
 template <typename T, int NI>
-__global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant__ CUtensorMap tmap,
-                                                          const PassArgs a) {
+__global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
+    k_pass(const __grid_constant__ CUtensorMap tmap, const PassArgs a) {
+  constexpr int kConsumers = PassCfg<NI>::C;
   using E = PassElem<T>;
+  // Each consumer lane owns runs of V consecutive columns (one 16-byte vector
+  // of the row in shared memory), NG runs in all, RS columns covered.
+  constexpr int V = 16 / (int)sizeof(T);
+  constexpr int NG = (NI * 32 + 32 * V - 1) / (32 * V);
+  constexpr int RS = NG * 32 * V;
   using acc_t = typename E::acc;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base_addr = smem_u32(smem_raw);
@@ -141,7 +174,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
   T* tiles = reinterpret_cast<T*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.region_bytes);
   uint64_t* empty = full + kMaxStages;
-  acc_t* vec_s = reinterpret_cast<acc_t*>(empty + kMaxStages);  // NI*32 values
+  acc_t* vec_s = reinterpret_cast<acc_t*>(empty + kMaxStages);  // RS values
   __shared__ int s_flag;       // 1 = skip the pass (done / error)
   __shared__ int s_abort;
   __shared__ double s_scal[2];
@@ -187,7 +220,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
       return;   // no TMA issued yet
     }
     const double ratio = a.start ? 0.0 : gam / a.scal->gam[a.gp];
-    for (int j = tid; j < NI * 32; j += blockDim.x) {
+    for (int j = tid; j < RS; j += blockDim.x) {
       double v = 0.0;
       if (j < a.d) v = a.z[j] + ratio * a.p_prev[j];
       vec_s[j] = (acc_t)v;
@@ -198,16 +231,21 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
       a.scal->iters += 1;
     }
   } else {
-    for (int j = tid; j < NI * 32; j += blockDim.x) vec_s[j] = (acc_t)((j < a.d) ? a.vec[j] : 0.0);
+    for (int j = tid; j < RS; j += blockDim.x) vec_s[j] = (acc_t)((j < a.d) ? a.vec[j] : 0.0);
   }
   __syncthreads();
 
   const int my_tiles =
       (blockIdx.x < a.ntiles) ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-  acc_t wacc[NI], wcmp[NI];
+  acc_t wv[NG][V], wb[E::compensated ? NG : 1][V], wc[E::compensated ? NG : 1][V];
 #pragma unroll
-  for (int i = 0; i < NI; ++i) wacc[i] = wcmp[i] = (acc_t)0;
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      wv[g][v] = (acc_t)0;
+      if constexpr (E::compensated) wb[g][v] = wc[g][v] = (acc_t)0;
+    }
   int issued = 0, skipped = -1;   // producer thread (tid 0) only
 
   if (warp == 0) {
@@ -238,12 +276,22 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
     }
   } else {
     // ---- consumers: t = a_row . v (warp all-reduce), acc += t a_row ----
+    constexpr bool WIDE = NI >= 32 || sizeof(acc_t) == 8;   // p and the row from shared memory
+    constexpr int RW = (sizeof(acc_t) == 4 && !WIDE) ? 2 : 1;   // rows in flight per warp
+    constexpr int FLUSH = 8;                                     // tiles per compensated flush
     const int cw = warp - 1;
-    int off[NI];
+    int off[NG];
 #pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      const int c = lane + 32 * i;
-      off[i] = (c < a.d) ? (c / a.boxc) * (int)a.slot_elems + (c % a.boxc) : -1;
+    for (int g = 0; g < NG; ++g) {
+      const int c0 = g * 32 * V + lane * V;
+      off[g] = (c0 < a.d) ? (c0 / a.boxc) * (int)a.slot_elems + (c0 % a.boxc) : -1;
+    }
+    acc_t pv[WIDE ? 1 : NG][V];
+    if constexpr (!WIDE) {
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int v = 0; v < V; ++v) pv[g][v] = vec_s[g * 32 * V + lane * V + v];
     }
     for (int k = 0; k < my_tiles; ++k) {
       const int s = k % a.stages;
@@ -255,30 +303,69 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
       const int tile = blockIdx.x + k * gridDim.x;
       const int64_t row0 = (int64_t)tile * a.tm;
       const T* st = tiles + (size_t)s * a.stage_elems;
-      for (int rr = cw; rr < a.tm; rr += kConsumers) {
+      for (int rr = cw; rr < a.tm; rr += RW * kConsumers) {
         if (row0 + rr >= a.m) break;
-        const T* rowp = st + rr * a.boxc;
-        acc_t t = (acc_t)0;
+        const T* rowp[RW];
+        bool live[RW];
 #pragma unroll
-        for (int i = 0; i < NI; ++i)
-          if (off[i] >= 0) t = fma(E::load(rowp[off[i]]), vec_s[lane + 32 * i], t);
-        t = warp_allsum(t);
-        if (a.mode == PASS_RESID) t = (acc_t)a.b[row0 + rr] - t;
+        for (int q = 0; q < RW; ++q) {
+          const int rq = rr + q * kConsumers;
+          live[q] = (q == 0) || (rq < a.tm && row0 + rq < a.m);
+          rowp[q] = st + (live[q] ? rq : rr) * a.boxc;
+        }
+        acc_t xr[WIDE ? 1 : RW][WIDE ? 1 : NG][V];
+        acc_t t[RW];
 #pragma unroll
-        for (int i = 0; i < NI; ++i) {
-          if (off[i] < 0) continue;
-          const acc_t x = E::load(rowp[off[i]]);
-          if constexpr (E::compensated) {
-            const acc_t pr = t * x;
-            const acc_t pe = fma(t, x, -pr);          // exact product error
-            const acc_t sm = wacc[i] + pr;
-            const acc_t bb = sm - wacc[i];
-            const acc_t se = (wacc[i] - (sm - bb)) + (pr - bb);   // exact sum error
-            wacc[i] = sm;
-            wcmp[i] += pe + se;
-          } else {
-            wacc[i] = fma(t, x, wacc[i]);
+        for (int q = 0; q < RW; ++q) t[q] = (acc_t)0;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          if (off[g] < 0) continue;
+#pragma unroll
+          for (int q = 0; q < RW; ++q) {
+            acc_t x[V];
+            E::load_vec(rowp[q] + off[g], x);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const acc_t pp = WIDE ? vec_s[g * 32 * V + lane * V + v] : pv[WIDE ? 0 : g][v];
+              t[q] = fma(x[v], pp, t[q]);
+              if constexpr (!WIDE) xr[q][g][v] = x[v];
+            }
           }
+        }
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+          t[q] = warp_allsum(t[q]);
+          if (a.mode == PASS_RESID) t[q] = (acc_t)a.b[row0 + rr + q * kConsumers] - t[q];
+          if (!live[q]) t[q] = (acc_t)0;
+        }
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          if (off[g] < 0) continue;
+#pragma unroll
+          for (int q = 0; q < RW; ++q) {
+            acc_t x[V];
+            if constexpr (WIDE) E::load_vec(rowp[q] + off[g], x);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const acc_t xx = WIDE ? x[v] : xr[WIDE ? 0 : q][WIDE ? 0 : g][v];
+              wv[g][v] = fma(t[q], xx, wv[g][v]);
+            }
+          }
+        }
+      }
+      if constexpr (E::compensated) {
+        // fold the block sums into the compensated accumulator (TwoSum)
+        if ((k % FLUSH) == FLUSH - 1 || k == my_tiles - 1) {
+#pragma unroll
+          for (int g = 0; g < NG; ++g)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const acc_t sm = wb[g][v] + wv[g][v];
+              const acc_t bb = sm - wb[g][v];
+              wc[g][v] += (wb[g][v] - (sm - bb)) + (wv[g][v] - bb);
+              wb[g][v] = sm;
+              wv[g][v] = (acc_t)0;
+            }
         }
       }
       __syncwarp();
@@ -298,18 +385,24 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass(const __grid_constant_
   __syncthreads();
 
   // ---- CTA partial: fixed-order sum over the consumer warps ----
-  double* red = reinterpret_cast<double*>(smem);   // reuse stage memory: kConsumers x (NI*32)
+  double* red = reinterpret_cast<double*>(smem);   // reuse stage memory: kConsumers x RS
   if (warp > 0) {
 #pragma unroll
-    for (int i = 0; i < NI; ++i)
-      red[(warp - 1) * NI * 32 + lane + 32 * i] = (double)wacc[i] + (double)wcmp[i];
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        double val;
+        if constexpr (E::compensated) val = ((double)wb[g][v] + (double)wc[g][v]) + (double)wv[g][v];
+        else val = (double)wv[g][v];
+        red[(size_t)(warp - 1) * RS + g * 32 * V + lane * V + v] = val;
+      }
   }
   __syncthreads();
   for (int j = tid; j < a.d; j += blockDim.x) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kConsumers; ++w) s += red[w * NI * 32 + j];
-    a.partials[(size_t)blockIdx.x * a.ldp + j] = s;
+    double sum = 0.0;
+#pragma unroll 4
+    for (int w = 0; w < kConsumers; ++w) sum += red[(size_t)w * RS + j];
+    a.partials[(size_t)blockIdx.x * a.ldp + j] = sum;
   }
 }
 
@@ -519,11 +612,12 @@ spcg_status make_pass_geom_t(const void* A, int64_t m, int d, int64_t lda, int d
   g->stages = stages;
   g->stage_bytes = stage;
   const size_t ni32 = (size_t)ni_for(d) * 32;
-  size_t red = (size_t)kConsumers * ni32 * 8;
+  const size_t cover = ni32 > 256 ? ni32 : 256;   // columns a consumer warp covers
+  size_t red = (size_t)kConsumers * cover * 8;
   size_t tiles = stage * stages;
   if (tiles < red) tiles = red;
   g->region_bytes = tiles;
-  g->smem_bytes = 128 + tiles + 2 * kMaxStages * 8 + ni32 * 8;
+  g->smem_bytes = 128 + tiles + 2 * kMaxStages * 8 + cover * 8;
   EncodeTiledFn enc = get_encode();
   if (!enc) return SPCG_E_CUDA;
   cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)m};
@@ -550,7 +644,7 @@ static spcg_status launch_pass_ni(spcg_ctx* c, const PassGeom& g, const PassArgs
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1));
   if (e0) SPCG_CK(cudaEventRecord(e0, c->stream));
-  k_pass<T, NI><<<grid, kPassThreads, g.smem_bytes, c->stream>>>(g.tmap, a);
+  k_pass<T, NI><<<grid, PassCfg<NI>::THREADS, g.smem_bytes, c->stream>>>(g.tmap, a);
   SPCG_CK(cudaGetLastError());
   if (e1) SPCG_CK(cudaEventRecord(e1, c->stream));
   c->n_launch += 1;
@@ -688,7 +782,7 @@ static spcg_status launch_gram_scratch_ni(const PassGeom& g, const PassArgs& a, 
                                           cudaStream_t st) {
   SPCG_CK(cudaFuncSetAttribute(k_pass<double, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)g.smem_bytes));
-  k_pass<double, NI><<<grid, kPassThreads, g.smem_bytes, st>>>(g.tmap, a);
+  k_pass<double, NI><<<grid, PassCfg<NI>::THREADS, g.smem_bytes, st>>>(g.tmap, a);
   SPCG_CK(cudaGetLastError());
   return SPCG_OK;
 }
@@ -804,6 +898,270 @@ spcg_status launch_features(spcg_ctx* c, const double* beta, float* dev_out2) {
   SPCG_CK(cudaGetLastError());
   c->n_launch += 2;
   return SPCG_OK;
+}
+
+}  // namespace spcg
+
+namespace spcg {
+
+// ---------------------------------------------------------------------------
+// The true gradient g = X^T (b - X beta) of the mixed-precision path from the
+// FP32 split X = Xh + Xl (|X - Xh - Xl| <= 2^-48 |X|), in double-FP32
+// arithmetic: products by TwoProd (FMA), sums by TwoSum, beta and b split
+// into FP32 pairs.  Every FP64 value of X is read as 8 bytes of FP32 pairs,
+// so the pass streams at memory speed instead of the FP64 pipe's rate, with
+// an error near 2^-44 relative instead of 2^-53 -- far below the 1e-6 target.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ts(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <int NI>
+__global__ void __launch_bounds__(32 * 9, 1)
+    k_pass_df(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUtensorMap tml,
+              const PassArgs a) {
+  constexpr int KC = 8;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t base_addr = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((128u - (base_addr & 127u)) & 127u);
+  float* tiles = reinterpret_cast<float*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.region_bytes);
+  uint64_t* empty = full + kMaxStages;
+  float* bh_s = reinterpret_cast<float*>(empty + kMaxStages);
+  float* bl_s = bh_s + NI * 32;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (a.scal->status != 0 || a.scal->done != 0) return;
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], KC);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  for (int j = tid; j < NI * 32; j += blockDim.x) {
+    const double v = (j < a.d) ? a.vec[j] : 0.0;
+    const float h = (float)v;
+    bh_s[j] = h;
+    bl_s[j] = (float)(v - (double)h);
+  }
+  __syncthreads();
+  const int my_tiles = (blockIdx.x < a.ntiles) ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  float wacc[NI], wcmp[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) wacc[i] = wcmp[i] = 0.f;
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int k = 0; k < my_tiles; ++k) {
+        const int s = k % a.stages;
+        if (k >= a.stages && !mbar_wait_bounded(&empty[s], ((k / a.stages) - 1) & 1, a.spin)) {
+          atomicExch(&a.scal->status, DEV_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        if (*(volatile int*)&s_abort) break;
+        issued = k + 1;
+        const int tile = blockIdx.x + k * gridDim.x;
+        mbar_expect_tx(&full[s], a.tx_bytes);
+        float* dst = tiles + (size_t)s * a.stage_elems;
+        for (int bx = 0; bx < a.nbox; ++bx) {
+          tma_load_2d(dst + (size_t)bx * a.slot_elems, &tmh, bx * a.boxc, tile * a.tm, &full[s]);
+          tma_load_2d(dst + (size_t)(a.nbox + bx) * a.slot_elems, &tml, bx * a.boxc, tile * a.tm,
+                      &full[s]);
+        }
+      }
+    }
+  } else {
+    const int cw = warp - 1;
+    int off[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int c = lane + 32 * i;
+      off[i] = (c < a.d) ? (c / a.boxc) * (int)a.slot_elems + (c % a.boxc) : -1;
+    }
+    const int lo_off = a.nbox * (int)a.slot_elems;
+    for (int k = 0; k < my_tiles; ++k) {
+      const int s = k % a.stages;
+      if (!mbar_wait_bounded(&full[s], (k / a.stages) & 1, a.spin)) {
+        atomicExch(&a.scal->status, DEV_TIMEOUT);
+        s_abort = 1;
+        break;
+      }
+      const int tile = blockIdx.x + k * gridDim.x;
+      const int64_t row0 = (int64_t)tile * a.tm;
+      const float* st = tiles + (size_t)s * a.stage_elems;
+      for (int rr = cw; rr < a.tm; rr += KC) {
+        if (row0 + rr >= a.m) break;
+        const float* rh = st + rr * a.boxc;
+        const float* rl = rh + lo_off;
+        float sh = 0.f, sl = 0.f;   // x . beta in double-FP32
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          if (off[i] < 0) continue;
+          const float xh = rh[off[i]], xl = rl[off[i]];
+          const int c = lane + 32 * i;
+          const float p = xh * bh_s[c];
+          const float pe = fmaf(xh, bh_s[c], -p);
+          float s2, se;
+          ts(sh, p, s2, se);
+          sh = s2;
+          sl += pe + se + fmaf(xh, bl_s[c], xl * bh_s[c]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+          const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+          float s2, se;
+          ts(sh, oh, s2, se);
+          sh = s2;
+          sl += ol + se;
+        }
+        // t = b - x . beta, as the pair (th, tl)
+        const double bv = a.b[row0 + rr];
+        const float b_h = (float)bv, b_l = (float)(bv - (double)b_h);
+        float th, tl;
+        ts(b_h, -sh, th, tl);
+        tl += b_l - sl;
+        const float t2 = th + tl;
+        tl = tl - (t2 - th);
+        th = t2;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          if (off[i] < 0) continue;
+          const float xh = rh[off[i]], xl = rl[off[i]];
+          const float p = th * xh;
+          const float pe = fmaf(th, xh, -p);
+          float s2, se;
+          ts(wacc[i], p, s2, se);
+          wacc[i] = s2;
+          wcmp[i] += pe + se + fmaf(th, xl, tl * xh);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+  }
+  __syncthreads();
+  if (s_abort && tid == 0) {
+    const int first = issued > a.stages ? issued - a.stages : 0;
+    for (int k = first; k < issued; ++k)
+      (void)mbar_wait_bounded(&full[k % a.stages], (k / a.stages) & 1, 1ll << 31);
+  }
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(smem);
+  if (warp > 0) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+      red[(warp - 1) * NI * 32 + lane + 32 * i] = (double)wacc[i] + (double)wcmp[i];
+  }
+  __syncthreads();
+  for (int j = tid; j < a.d; j += blockDim.x) {
+    double sum = 0.0;
+    for (int w = 0; w < KC; ++w) sum += red[w * NI * 32 + j];
+    a.partials[(size_t)blockIdx.x * a.ldp + j] = sum;
+  }
+}
+
+// Geometry of the hi/lo pair pass: FP32 boxes for both halves in one stage.
+spcg_status make_pass_geom_df(const float* Xh, const float* Xl, int64_t m, int d, int64_t lda,
+                              PassGeom* g, CUtensorMap* tml) {
+  SPCG_TRY(make_pass_geom_t(Xl, m, d, lda, DT_F32, g));
+  *tml = g->tmap;
+  PassGeom h;
+  // half the rows per tile: each stage carries both halves
+  SPCG_TRY(make_pass_geom_t(Xh, m, d, lda, DT_F32, &h));
+  int tm = h.tm > 1 ? h.tm / 2 : 1;
+  if (tm > 8) tm &= ~7;
+  const int bc = h.boxc;
+  EncodeTiledFn enc = get_encode();
+  cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)(lda * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)bc, (cuuint32_t)tm};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r1 = enc(&h.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Xh), dims,
+                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = enc(tml, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Xl), dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return SPCG_E_CUDA;
+  h.tm = tm;
+  h.ntiles = (int)((m + tm - 1) / tm);
+  const size_t slot = (((size_t)tm * bc * 4) + 127) & ~(size_t)127;
+  const size_t stage = slot * h.nbox * 2;
+  int stages = (int)((192 * 1024) / stage);
+  if (stages > kMaxStages) stages = kMaxStages;
+  if (stages < 2) stages = 2;
+  h.stages = stages;
+  h.stage_bytes = stage;
+  const size_t ni32 = (size_t)ni_for(d) * 32;
+  size_t red = (size_t)8 * ni32 * 8;
+  size_t tiles = stage * stages;
+  if (tiles < red) tiles = red;
+  h.region_bytes = tiles;
+  h.smem_bytes = 128 + tiles + 2 * kMaxStages * 8 + 2 * ni32 * 4;
+  h.dtype = DT_F32;
+  h.esize = 8;   // algorithmic bytes per element (the pair)
+  *g = h;
+  return SPCG_OK;
+}
+
+template <int NI>
+static spcg_status launch_df_ni(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml,
+                                const PassArgs& a, int grid) {
+  SPCG_CK(cudaFuncSetAttribute(k_pass_df<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)g.smem_bytes));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1));
+  if (e0) SPCG_CK(cudaEventRecord(e0, c->stream));
+  k_pass_df<NI><<<grid, 32 * 9, g.smem_bytes, c->stream>>>(g.tmap, tml, a);
+  SPCG_CK(cudaGetLastError());
+  if (e1) SPCG_CK(cudaEventRecord(e1, c->stream));
+  c->n_launch += 1;
+  c->n_pass += 1;
+  c->pass_bytes += (uint64_t)g.m * g.d * 8;
+  return SPCG_OK;
+}
+
+spcg_status pass_resid_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml,
+                          const double* b, const double* x) {
+  int grid = c->pb.grid;
+  if (grid > g.ntiles) grid = g.ntiles;
+  if (grid < 1) grid = 1;
+  PassArgs a{};
+  a.mode = PASS_RESID;
+  a.vec = x;
+  a.b = b;
+  a.m = g.m;
+  a.d = g.d;
+  a.nbox = g.nbox;
+  a.boxc = g.boxc;
+  a.tm = g.tm;
+  a.ntiles = g.ntiles;
+  a.stages = g.stages;
+  a.tx_bytes = (uint32_t)((size_t)2 * g.nbox * g.boxc * g.tm * 4);
+  a.slot_elems = (uint32_t)(g.stage_bytes / (2 * g.nbox) / 4);
+  a.stage_elems = (uint32_t)(g.stage_bytes / 4);
+  a.region_bytes = (uint32_t)g.region_bytes;
+  a.partials = c->pb.partials;
+  a.ldp = c->pb.ldp;
+  a.scal = c->scal;
+  a.spin = c->opts.spin_budget > 0 ? c->opts.spin_budget : (1ll << 31);
+  c->pb.last_grid = grid;
+  switch (ni_for(g.d)) {
+    case 1: return launch_df_ni<1>(c, g, tml, a, grid);
+    case 2: return launch_df_ni<2>(c, g, tml, a, grid);
+    case 4: return launch_df_ni<4>(c, g, tml, a, grid);
+    case 8: return launch_df_ni<8>(c, g, tml, a, grid);
+    case 16: return launch_df_ni<16>(c, g, tml, a, grid);
+    case 32: return launch_df_ni<32>(c, g, tml, a, grid);
+    default: return SPCG_E_INVALID_ARG;
+  }
 }
 
 }  // namespace spcg

@@ -86,57 +86,63 @@ __global__ void __launch_bounds__(QR_WARPS * 32)
 // result does not depend on timing.  The cluster barrier is the hardware
 // barrier of the thread-block cluster (no software spin).
 constexpr int QRC = 8;            // CTAs per cluster
-constexpr int QRC_WARPS = 8;
+constexpr int QRC_WARPS = 16;
 constexpr int QRC_MAXCOLS = 128;  // trailing columns per cluster per step
+constexpr int QRC_MAXCHUNK = 4096;  // rows of the reflector a CTA stages in shared memory
 
+// The CTA's rows of column k (the reflector, v_0 replacing x_k) are staged in
+// shared memory, so the update loop streams only the trailing column through
+// global memory and its loads overlap (no aliasing with the reflector).
 __global__ void __cluster_dims__(QRC, 1, 1) __launch_bounds__(QRC_WARPS * 32)
     k_householder_cluster(double* __restrict__ A, int64_t r, int d, int k,
                           double* __restrict__ Rdiag) {
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
   const int ncl = gridDim.x / QRC, cl = blockIdx.x / QRC;
+  extern __shared__ double vs[];   // chunk of column k
   __shared__ double part_s2;
   __shared__ double pdot[QRC_MAXCOLS];
   __shared__ double red[QRC_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double* colk = A + (int64_t)k * r;
+  const double* colk = A + (int64_t)k * r + k;          // colk[i] = x_{k+i}
   const int64_t len = r - k;
   const int64_t chunk = (len + QRC - 1) / QRC;
-  const int64_t lo = q * chunk;                         // rows k+lo .. k+hi-1
+  const int64_t lo = q * chunk;
   const int64_t hi = (lo + chunk < len) ? lo + chunk : len;
+  const int64_t n = hi > lo ? hi - lo : 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) vs[i] = colk[lo + i];
+  __syncthreads();
   // share of sum x_i^2 over rows k+1..r-1
   double s2 = 0.0;
-  for (int64_t i = (lo > 1 ? lo : 1) + threadIdx.x; i < hi; i += blockDim.x) {
-    const double x = colk[k + i];
-    s2 = fma(x, x, s2);
-  }
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    if (lo + i > 0) s2 = fma(vs[i], vs[i], s2);
   s2 = block_sum<QRC_WARPS>(s2, red);
   if (threadIdx.x == 0) part_s2 = s2;
   cluster.sync();
   double tot = 0.0;
   for (int rr = 0; rr < QRC; ++rr) tot += *cluster.map_shared_rank(&part_s2, rr);
-  const double x0 = colk[k];
+  const double x0 = colk[0];
   const double normx = sqrt(x0 * x0 + tot);
   const double alpha = (x0 >= 0.0) ? -normx : normx;
   const double v0 = x0 - alpha;
   const double vv = v0 * v0 + tot;
   if (blockIdx.x == 0 && threadIdx.x == 0) Rdiag[k] = alpha;
+  if (lo == 0 && n > 0 && threadIdx.x == 0) vs[0] = v0;   // the reflector's first entry
+  __syncthreads();
   const int ncols = d - k - 1;
-  // this cluster's columns: j = k + 1 + cl + c * ncl, c = 0, 1, ...
   const int mycols = ncols > cl ? (ncols - cl + ncl - 1) / ncl : 0;
   if (vv != 0.0) {
     for (int c = warp; c < mycols; c += QRC_WARPS) {
-      const double* cj = A + (int64_t)(k + 1 + cl + c * ncl) * r + k;
+      const double* cj = A + (int64_t)(k + 1 + cl + c * ncl) * r + k + lo;
       double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-      int64_t i = lo + lane;
-      for (; i + 96 < hi; i += 128) {
-        const double va = (i == 0) ? v0 : colk[k + i];
-        p0 = fma(va, cj[i], p0);
-        p1 = fma(colk[k + i + 32], cj[i + 32], p1);
-        p2 = fma(colk[k + i + 64], cj[i + 64], p2);
-        p3 = fma(colk[k + i + 96], cj[i + 96], p3);
+      int64_t i = lane;
+      for (; i + 96 < n; i += 128) {
+        p0 = fma(vs[i], cj[i], p0);
+        p1 = fma(vs[i + 32], cj[i + 32], p1);
+        p2 = fma(vs[i + 64], cj[i + 64], p2);
+        p3 = fma(vs[i + 96], cj[i + 96], p3);
       }
-      for (; i < hi; i += 32) p0 = fma((i == 0) ? v0 : colk[k + i], cj[i], p0);
+      for (; i < n; i += 32) p0 = fma(vs[i], cj[i], p0);
       const double p = warp_allsum((p0 + p1) + (p2 + p3));
       if (lane == 0) pdot[c] = p;
     }
@@ -148,9 +154,16 @@ __global__ void __cluster_dims__(QRC, 1, 1) __launch_bounds__(QRC_WARPS * 32)
       double sj = 0.0;
       for (int rr = 0; rr < QRC; ++rr) sj += *cluster.map_shared_rank(&pdot[c], rr);
       const double f = tau * sj;
-      double* cj = A + (int64_t)(k + 1 + cl + c * ncl) * r + k;
-      for (int64_t i = lo + lane; i < hi; i += 32)
-        cj[i] = fma(-f, (i == 0) ? v0 : colk[k + i], cj[i]);
+      double* cj = A + (int64_t)(k + 1 + cl + c * ncl) * r + k + lo;
+      int64_t i = lane;
+      for (; i + 96 < n; i += 128) {
+        const double c0 = cj[i], c1 = cj[i + 32], c2 = cj[i + 64], c3 = cj[i + 96];
+        cj[i] = fma(-f, vs[i], c0);
+        cj[i + 32] = fma(-f, vs[i + 32], c1);
+        cj[i + 64] = fma(-f, vs[i + 64], c2);
+        cj[i + 96] = fma(-f, vs[i + 96], c3);
+      }
+      for (; i < n; i += 32) cj[i] = fma(-f, vs[i], cj[i]);
     }
   }
   cluster.sync();   // no CTA leaves while another still reads its shared memory
@@ -221,7 +234,11 @@ spcg_status launch_precond_factor(spcg_ctx* c) {
   const int64_t r = s.sched.r;
   int ncl = c->num_sms / QRC;
   if (ncl < 1) ncl = 1;
-  const bool use_cluster = ((d - 1 + ncl - 1) / ncl) <= QRC_MAXCOLS;
+  const bool use_cluster = ((d - 1 + ncl - 1) / ncl) <= QRC_MAXCOLS &&
+                           (r + QRC - 1) / QRC <= QRC_MAXCHUNK;
+  if (use_cluster)
+    SPCG_CK(cudaFuncSetAttribute(k_householder_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(QRC_MAXCHUNK * sizeof(double))));
   const size_t stage_cap = 200 * 1024;
   const int staged = (size_t)r * 8 <= stage_cap;
   if (!use_cluster && staged)
@@ -232,7 +249,9 @@ spcg_status launch_precond_factor(spcg_ctx* c) {
     if (use_cluster) {
       int g = cols < ncl ? cols : ncl;   // clusters with at least one column
       if (g < 1) g = 1;
-      k_householder_cluster<<<g * QRC, QRC_WARPS * 32, 0, c->stream>>>(s.Ahat, r, d, k, s.Rdiag);
+      const size_t chunk_bytes = (size_t)((r - k + QRC - 1) / QRC) * sizeof(double);
+      k_householder_cluster<<<g * QRC, QRC_WARPS * 32, chunk_bytes, c->stream>>>(s.Ahat, r, d, k,
+                                                                                s.Rdiag);
     } else {
       int grid = (cols + QR_WARPS - 1) / QR_WARPS;
       if (grid < 1) grid = 1;
