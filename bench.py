@@ -30,6 +30,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    "c3": dict(name="mixed precision, N=2^22, d=1000, kappa=1e8, rows scaled by |t_3| before "
+                    "orthonormalising, sigma=1, seed=1",
+               N=1 << 22, d=1000, kappa=1e8, sigma=1.0, seed=1, tol=1e-6, leverage_df=3),
+    "c4": dict(name="batched: 512 problems, N ~ U[2^12, 2^17], d ~ U[16, 256], X iid N(0,1) "
+                    "times column scales log-uniform in [1e-3, 1e3], sigma=1, FP32, seed=1",
+               N=None, d=None, kappa=None, sigma=1.0, seed=1, tol=1e-6, batch=512),
+    "c5": dict(name="learned schedule: N=2^23, d=256, kappa=1e4, sigma=0.5, seed=1",
+               N=1 << 23, d=256, kappa=1e4, sigma=0.5, seed=1, tol=1e-6),
     "c2": dict(name="plain SPCG FP64, N=2^20, d=500, kappa=1e6, sigma=0.1, seed=1",
                N=1 << 20, d=500, kappa=1e6, sigma=0.1, seed=1, tol=1e-6),
     "c1": dict(name="plain SPCG FP64, N=20000, d=50, X iid N(0,1), sigma=1, seed=1",
@@ -45,7 +53,200 @@ def make_problem(w, N=None, seed_offset=0):
     N = N or w["N"]
     if w["kappa"] is None:
         return gaussian_problem(N, w["d"], w["sigma"], seed=w["seed"] + seed_offset)
-    return svd_problem(N, w["d"], w["kappa"], w["sigma"], seed=w["seed"] + seed_offset)
+    return svd_problem(N, w["d"], w["kappa"], w["sigma"], seed=w["seed"] + seed_offset,
+                       leverage_df=w.get("leverage_df"))
+
+
+def base_line(args, w, value_s, metric, dtype, world=1):
+    return {"metric": metric, "value": value_s, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value_s * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": w["name"]}}
+
+
+def time_solves(solver, seed, sched, steps, warmup, stream, fn=None):
+    import torch
+    fn = fn or (lambda: solver.solve(seed, sched))
+    for _ in range(warmup):
+        fn()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    outs = [fn() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, outs
+
+
+def run_forms(args, w):
+    """Plain FP64 vs mixed precision on one large problem (C3)."""
+    import torch
+
+    from oracle.linalg import ols_lowmem
+    from oracle.metrics import rel_pred_error
+    from paper_2607_25272_b300 import spcg as S
+    t0 = time.time()
+    X, Y, _ = make_problem(w)
+    gen_s = time.time() - t0
+    N, d = X.shape
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    Xd = torch.from_numpy(X).to(dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    sched = S.spcg_default_schedule(N, d)
+    sched.tol = w["tol"]
+    sched.max_restarts = 20
+    res = {}
+    for name, prec in (("plain_fp64", S.PREC_FP64), ("mixed", S.PREC_MIXED)):
+        o = S.Opts()
+        o.precision = prec
+        sv = S.Solver(Xd, Yd, o)
+        ms, outs = time_solves(sv, w["seed"], sched, args.steps, args.warmup, stream,
+                               fn=lambda sv=sv: sv.solve(w["seed"], sched, raise_on_error=False))
+        beta, info, st = outs[-1]
+        o.profile = 1
+        pv = S.Solver(Xd, Yd, o)
+        _, pinfo, _ = pv.solve(w["seed"], sched, raise_on_error=False)
+        pv.close()
+        res[name] = {"s": ms / 1e3, "status": S.STATUS[st], "beta": beta.cpu().numpy(),
+                     "phases_ms": {"sketch": info.ms_sketch, "stages": info.ms_stages,
+                                   "refine": info.ms_refine},
+                     "refine_iters": info.refine_iters, "restarts": info.restarts,
+                     "pass_gbs": pinfo.bytes_pass / (pinfo.pass_ms / 1e3) / 1e9
+                     if pinfo.pass_ms > 0 else None}
+        sv.close()
+    t1 = time.time()
+    bh = ols_lowmem(X, Y)
+    ols_s = time.time() - t1
+    for name in res:
+        res[name]["rel_pred_error"] = rel_pred_error(X, res[name].pop("beta"), bh)
+    line = base_line(args, w, res["mixed"]["s"],
+                     "seconds to 1e-6 OLS prediction error (mixed precision vs plain FP64 SPCG)",
+                     "bf16/f32/f64")
+    line["config"].update({"N": N, "d": d, "tol": w["tol"]})
+    line["forms"] = res
+    line["speedup_mixed_vs_plain_fp64"] = res["plain_fp64"]["s"] / res["mixed"]["s"]
+    line["host_s"] = {"generate": gen_s, "oracle_ols": ols_s}
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args, w):
+    """C4: 512 uneven FP32 problems in one persistent launch vs a loop of
+    single plain-FP64 solves of the same problems."""
+    import torch
+
+    from oracle.linalg import ols
+    from oracle.metrics import rel_pred_error
+    from paper_2607_25272_b300 import spcg as S
+    from paper_2607_25272_b300.inputs import scaled_columns_problem
+    rng = np.random.default_rng(w["seed"])
+    n = w["batch"]
+    probs = []
+    for i in range(n):
+        N = int(rng.integers(1 << 12, (1 << 17) + 1))
+        d = int(rng.integers(16, 257))
+        X, Y, _ = scaled_columns_problem(N, d, 1e-3, 1e3, w["sigma"], seed=w["seed"] * 100000 + i)
+        probs.append((X.astype(np.float32), Y.astype(np.float32)))
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    Xs, Ys = [], []
+    for X, Y in probs:
+        N, d = X.shape
+        ld = (d + 3) // 4 * 4
+        Xd = torch.zeros((N, ld), dtype=torch.float32, device=dev)
+        Xd[:, :d] = torch.from_numpy(X).to(dev)
+        Xs.append(Xd[:, :d])
+        Ys.append(torch.from_numpy(Y).to(dev))
+    B = S.Batch(Xs, Ys)
+    tiles = B.autotune(w["seed"], w["tol"])
+    for _ in range(args.warmup):
+        B.solve(w["seed"], w["tol"])
+    times = []
+    for _ in range(args.steps):
+        rc, st, it, ms = B.solve(w["seed"], w["tol"])
+        times.append(ms)
+    ms_b = float(np.median(times))
+    betas = [b.cpu().numpy() for b in B.betas]
+    B.close()
+    # the comparator: one plain FP64 spcg_solve per problem, back to back
+    loop_ms = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    loop_status = []
+    for (X, Y), Xd in zip(probs, Xs):
+        X64 = torch.from_numpy(X.astype(np.float64)).to(dev)
+        Y64 = torch.from_numpy(Y.astype(np.float64)).to(dev)
+        sv = S.Solver(X64, Y64)
+        sc = S.spcg_default_schedule(*X.shape)
+        sc.tol = w["tol"]
+        sv.solve(w["seed"], sc, raise_on_error=False)          # warm
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, _, st_ = sv.solve(w["seed"], sc, raise_on_error=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        loop_ms += e0.elapsed_time(e1)
+        loop_status.append(st_)
+        sv.close()
+    errs = []
+    for (X, Y), b in zip(probs, betas):
+        X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+        errs.append(rel_pred_error(X64, b, ols(X64, Y64)))
+    line = base_line(args, w, ms_b / 1e3,
+                     "seconds to 1e-6 OLS prediction error for the whole batch (batched vs a "
+                     "loop of plain FP64 SPCG solves)", "f32 (compensated) / f64 scalars")
+    line["config"].update({"problems": n, "tol": w["tol"]})
+    line["batched"] = {"s": ms_b / 1e3, "status_ok": int(sum(1 for v in st if v == 0)),
+                       "max_rel_pred_error": float(max(errs)),
+                       "problems_meeting_tol": int(sum(1 for e in errs if e <= w["tol"])),
+                       "autotuned_chunk_bytes": tiles}
+    line["loop_plain_fp64"] = {"s": loop_ms / 1e3,
+                               "status_ok": int(sum(1 for v in loop_status if v == 0))}
+    line["speedup_batched_vs_loop"] = loop_ms / ms_b if ms_b > 0 else None
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args, w):
+    """C5: the learned schedule vs the paper's schedule (plain FP64 SPCG)."""
+    import torch
+
+    from oracle.linalg import ols_lowmem
+    from oracle.metrics import rel_pred_error
+    from paper_2607_25272_b300 import schedule_model as SM
+    from paper_2607_25272_b300 import spcg as S
+    X, Y, _ = make_problem(w)
+    N, d = X.shape
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    Xd = torch.from_numpy(X).to(dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    Wb, norm = SM.load(args.weights) if args.weights else SM.load()
+    sv = S.Solver(Xd, Yd)
+    ms_p, outs_p = time_solves(sv, w["seed"], None, args.steps, args.warmup, stream,
+                               fn=lambda: sv.solve_learned(w["seed"], None, None, w["tol"],
+                                                           raise_on_error=False))
+    ms_l, outs_l = time_solves(sv, w["seed"], None, args.steps, args.warmup, stream,
+                               fn=lambda: sv.solve_learned(w["seed"], Wb, norm, w["tol"],
+                                                           raise_on_error=False))
+    bp, ip, cp, sp = outs_p[-1]
+    bl, il, cl, sl = outs_l[-1]
+    sv.close()
+    bh = ols_lowmem(X, Y)
+    line = base_line(args, w, ms_l / 1e3,
+                     "seconds to 1e-6 OLS prediction error (learned schedule vs the paper's "
+                     "schedule, plain FP64 SPCG)", "f64")
+    line["config"].update({"N": N, "d": d, "tol": w["tol"],
+                           "model": "MLP 4-64-64-25, BF16 weights" if Wb is not None else
+                           "no trained weights: paper schedule"})
+    line["paper_schedule"] = {"s": ms_p / 1e3, "candidate": cp, "status": S.STATUS[sp],
+                              "rel_pred_error": rel_pred_error(X, bp.cpu().numpy(), bh),
+                              "refine_iters": ip.refine_iters}
+    line["learned_schedule"] = {"s": ms_l / 1e3, "candidate": cl, "status": S.STATUS[sl],
+                                "rel_pred_error": rel_pred_error(X, bl.cpu().numpy(), bh),
+                                "refine_iters": il.refine_iters, "stages": il.K}
+    line["speedup_learned_vs_paper"] = ms_p / ms_l
+    print(json.dumps(line), flush=True)
 
 
 class ClockSampler:
@@ -103,6 +304,18 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(value, device=None):
+    """The largest per-rank value (the job's time); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -158,28 +371,66 @@ def run_pass_only(args, w, local_rank):
     g = torch.Generator(device=dev)
     g.manual_seed(1)
     m, d = args.rows, w["d"]
-    A = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g)
+    dt = getattr(torch, args.pass_dtype)
+    align = 16 // torch.empty(0, dtype=dt).element_size()     # rows 16-byte aligned (TMA)
+    ld = (d + align - 1) // align * align
+    A = torch.zeros((m, ld), dtype=dt, device=dev)
+    A[:, :d] = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g).to(dt)
+    A = A[:, :d]
     p = torch.randn(d, dtype=torch.float64, device=dev, generator=g)
     opts = S.Opts()
     opts.profile = 1
-    s = S.Solver(A[: d + 1], torch.zeros(d + 1, dtype=torch.float64, device=dev))
+    s = S.Solver(torch.randn((d + 2, d), dtype=torch.float64, device=dev, generator=g),
+                 torch.zeros(d + 2, dtype=torch.float64, device=dev))
     out = torch.empty(d, dtype=torch.float64, device=dev)
+    call = s.gram_apply if args.pass_dtype == "float64" else s.gram_apply_typed
     for _ in range(args.warmup):
-        s.gram_apply(A, p, out)
+        call(A, p, out)
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
-        s.gram_apply(A, p, out)
+        call(A, p, out)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    nbytes = m * d * 8
-    print(json.dumps({"kernel": "k_pass via spcg_gram_apply (pass + reduce + sync)",
+    nbytes = m * d * A.element_size()
+    print(json.dumps({"kernel": f"k_pass<{args.pass_dtype}> via spcg_gram_apply (pass + reduce + sync)",
                       "rows": m, "d": d, "ms_per_call": ms, "alg_bytes": nbytes,
                       "gbs": nbytes / ms / 1e6, "tflops": 4 * m * d / ms / 1e9}), flush=True)
+    s.close()
+
+
+def run_sketch_only(args, w, local_rank):
+    """spcg_sketch alone (column scales, transform, preconditioner QR) on a rows x d
+    problem drawn on the GPU."""
+    import torch
+
+    from paper_2607_25272_b300 import spcg as S
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1)
+    m, d = args.rows, w["d"]
+    X = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g)
+    Y = torch.randn(m, dtype=torch.float64, device=dev, generator=g)
+    s = S.Solver(X, Y)
+    sc = S.spcg_default_schedule(m, d)
+    for _ in range(args.warmup):
+        s.sketch(1, sc)
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.sketch(1, sc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": "spcg_sketch", "rows": m, "d": d,
+                      "ms_per_call": e0.elapsed_time(e1) / args.steps}), flush=True)
     s.close()
 
 
@@ -225,12 +476,32 @@ def run_ours(args, w, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     beta_h = beta.cpu().numpy()
+
+    # the mixed-precision form on the same problem and schedule (BF16 stages,
+    # FP32 compensated refinement, FP64 true gradients)
+    mopts = S.Opts()
+    mopts.precision = S.PREC_MIXED
+    msolver = S.Solver(Xd, Yd, mopts)
+    mbeta = torch.empty(d, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        msolver.solve(w["seed"], sched, mbeta)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    minfos = []
+    for _ in range(args.steps):
+        _, minfo, _ = msolver.solve(w["seed"], sched, mbeta)
+        minfos.append(minfo)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_mixed = e0.elapsed_time(e1) / args.steps
+    mbeta_h = mbeta.cpu().numpy()
+    mopts.profile = 1
+    mpsolver = S.Solver(Xd, Yd, mopts)
+    _, mpinfo, _ = mpsolver.solve(w["seed"], sched)
+    mpsolver.close()
+    msolver.close()
 
     # fused-pass timing: the same solves with CUDA events around every pass
     opts = S.Opts()
@@ -269,7 +540,9 @@ def run_ours(args, w, rank, world, local_rank):
         return
 
     # accuracy against the oracle's OLS estimator (outside the timed region)
-    e_rel = rel_pred_error(X, beta_h, ols(X, Y))
+    beta_ols = ols(X, Y)
+    e_rel = rel_pred_error(X, beta_h, beta_ols)
+    e_rel_mixed = rel_pred_error(X, mbeta_h, beta_ols)
 
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
@@ -310,6 +583,18 @@ def run_ours(args, w, rank, world, local_rank):
                      "converged": last.converged},
         "phases_ms": {"sketch": last.ms_sketch, "stages": last.ms_stages,
                       "refine": last.ms_refine},
+        "forms": {
+            "plain_fp64": {"s": ms / 1e3, "rel_pred_error": e_rel},
+            "mixed": {"s": ms_mixed / 1e3, "rel_pred_error": e_rel_mixed,
+                      "speedup_vs_plain_fp64": ms / ms_mixed,
+                      "phases_ms": {"sketch": minfos[-1].ms_sketch, "stages": minfos[-1].ms_stages,
+                                    "refine": minfos[-1].ms_refine},
+                      "refine_iters": minfos[-1].refine_iters, "restarts": minfos[-1].restarts,
+                      "pass_gbs": (mpinfo.bytes_pass / (mpinfo.pass_ms / 1e3) / 1e9)
+                      if mpinfo.pass_ms > 0 else None,
+                      "pass_hbm_frac": (mpinfo.bytes_pass / (mpinfo.pass_ms / 1e3) / 1e9
+                                        / measured_peaks().get("hbm_gbs", 6400.0))
+                      if mpinfo.pass_ms > 0 else None}},
         "gpu_launches": launches,
         "roofline": roofline,
         "e2e": {"value": float(np.median(t_e2e)) / 1e3, "unit": "s",
@@ -329,9 +614,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=[None, "pass"],
+    ap.add_argument("--kernel", default=None, choices=[None, "pass", "sketch"],
                     help="time one kernel alone instead of the solve")
     ap.add_argument("--rows", type=int, default=1 << 18)
+    ap.add_argument("--weights", default=None, help="schedule model weights (npz) for c5")
+    ap.add_argument("--pass-dtype", default="float64", choices=["float64", "float32", "bfloat16"])
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -342,6 +629,14 @@ def main():
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if args.kernel == "pass":
         run_pass_only(args, w, local_rank)
+    elif args.kernel == "sketch":
+        run_sketch_only(args, w, local_rank)
+    elif args.impl == "ours" and args.workload == "c3":
+        run_forms(args, w)
+    elif args.impl == "ours" and args.workload == "c4":
+        run_batched(args, w)
+    elif args.impl == "ours" and args.workload == "c5":
+        run_learned(args, w)
     elif args.impl == "reference":
         run_reference(args, w, rank, world)
     else:
