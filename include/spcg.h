@@ -57,13 +57,17 @@ enum {
   SPCG_PREC_FP64 = 0,       /* plain FP64 everywhere (the comparator path)    */
   SPCG_PREC_MIXED = 1       /* Stage I reads a BF16 copy of the sketched rows
                                with FP32 accumulation; Stage II iterates on an
-                               FP32 copy Xh of X with compensated (TwoProd/TwoSum)
-                               accumulation, and every true gradient
-                               X^T (Y - X beta) that the stopping rule trusts is
-                               computed in double-FP32 arithmetic from the split
-                               X = Xh + Xl (|X - Xh - Xl| <= 2^-48 |X|); the
-                               sketch, the QR giving R, R^{-1} and the CG scalars
-                               stay FP64                                       */
+                               FP32 copy Xh of X (FP32 row dot products, row
+                               sums folded into TwoSum-compensated accumulators)
+                               or, when the condition estimate
+                               says FP32 rows are too coarse (see
+                               spcg_opts.inner_prec), on the double-FP32 split
+                               X = Xh + Xl (|X - Xh - Xl| <= 2^-48 |X|); every
+                               true gradient X^T (Y - X beta) that the stopping
+                               rule trusts is computed in double-FP32 from that
+                               split or, for ill-conditioned X, by an FP64 pass
+                               (spcg_opts.grad_prec); the sketch, the QR giving
+                               R, R^{-1} and the CG scalars stay FP64          */
 };
 
 /*
@@ -112,8 +116,34 @@ typedef struct {
                                never issues its first row tile, so its wait
                                runs out (SPCG_E_TIMEOUT) without any fault      */
   int32_t profile;          /* 1 = time every fused pass with CUDA events      */
-  int32_t reserved[2];
+  int32_t inner_prec;       /* SPCG_PREC_MIXED only: operand of the Stage II
+                               iterations, SPCG_INNER_*; 0 = automatic        */
+  int32_t grad_prec;        /* SPCG_PREC_MIXED only: arithmetic of the true
+                               gradients, SPCG_GRAD_*; 0 = automatic          */
 } spcg_opts;
+
+/* Stage II operand of the mixed path (spcg_opts.inner_prec, spcg_info.inner_prec).
+ * Automatic choice: with nu the power-iteration estimate of ||D R^{-1}||_2,
+ * D = diag(||R e_j||) (spcg_info.cond_est), FP32 rows when 2^-24 nu <= 1/32,
+ * else the double-FP32 pair.  FP32 rounding perturbs the preconditioned
+ * operator by about 2^-24 nu; refinement on true gradients contracts only
+ * while that stays well below one. */
+enum {
+  SPCG_INNER_AUTO = 0,
+  SPCG_INNER_F32 = 1,       /* Xh, compensated FP32 (4 bytes per element)     */
+  SPCG_INNER_DF = 2         /* Xh + Xl in double-FP32 (8 bytes per element)   */
+};
+
+/* True gradients X^T (Y - X beta) of the mixed path (spcg_opts.grad_prec,
+ * spcg_info.grad_prec).  The stopping rule compares sqrt(g^T H-hat^{-1} g)
+ * with (tol/2) ||R beta||, and an error in g reaches that metric amplified by
+ * up to nu.  Automatic choice: the double-FP32 pass (about 2^-48 relative per
+ * term, read at memory speed) while 2^-48 nu <= tol/64, else the FP64 pass. */
+enum {
+  SPCG_GRAD_AUTO = 0,
+  SPCG_GRAD_F64 = 1,        /* FP64 pass over X                                */
+  SPCG_GRAD_DF = 2          /* double-FP32 pass over Xh + Xl                   */
+};
 
 typedef struct {
   int32_t K;
@@ -131,6 +161,12 @@ typedef struct {
   double pass_ms;           /* summed device time of the fused passes (CUDA
                                events around each launch; only when
                                spcg_opts.profile = 1, else 0)                  */
+  double cond_est;          /* mixed path: estimate of ||D R^{-1}||_2 (above);
+                               0 on the FP64 path                              */
+  int32_t inner_prec;       /* mixed path: SPCG_INNER_F32 or SPCG_INNER_DF as
+                               used by Stage II; 0 on the FP64 path            */
+  int32_t grad_prec;        /* SPCG_GRAD_F64 or SPCG_GRAD_DF: the arithmetic of
+                               the true gradients of Stage II                  */
 } spcg_info;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -273,12 +309,28 @@ spcg_status spcg_gram_apply(spcg_ctx* ctx, const double* A, int64_t m, int64_t l
 /*
  * The same pass on an FP32 (dtype 1) or BF16 (dtype 2) operand, the element
  * types the mixed-precision path streams (dtype 0 = FP64 as above).  FP32 rows
- * accumulate in FP32 with compensated products and sums; BF16 rows in plain
- * FP32; the products with p use p rounded to FP32.  lda * element size must
- * be a multiple of 16 bytes.  p, w: device FP64.
+ * form each row's dot product in FP32 and fold the row sums into a
+ * TwoSum-compensated accumulator; BF16 rows use plain FP32; the products with p use p rounded to FP32.  dtype 3 is the
+ * double-FP32 pair A = Ah + Al: the m x lda FP32 block Ah followed directly
+ * by the m x lda FP32 block Al (so Al starts at (float*)A + m * lda), with p
+ * split into an FP32 pair and every product and sum in double-FP32
+ * (TwoProd/TwoSum).  lda * element size (4 for dtype 3) must be a multiple
+ * of 16 bytes.  p, w: device FP64.
  */
 spcg_status spcg_gram_apply_typed(spcg_ctx* ctx, const void* A, int32_t dtype, int64_t m,
                                   int64_t lda, const double* p, double* w);
+
+/*
+ * The residual-mode pass, the true gradient of Sec. 2.2's stopping rule on
+ * caller data: g = A^T (b - A x), reading A once.  A and dtype as for
+ * spcg_gram_apply_typed (0 FP64, 1 FP32, 2 BF16, 3 double-FP32 pair); b:
+ * device m (FP64), x, g: device d (FP64).  FP64 rows compute in FP64; FP32
+ * and BF16 rows form b - a.x and accumulate in FP32 (FP32 rows with the
+ * compensated sums of spcg_gram_apply_typed); the pair in double-FP32 with b
+ * and x split into FP32 pairs.  m = 0 gives g = 0.
+ */
+spcg_status spcg_resid_apply_typed(spcg_ctx* ctx, const void* A, int32_t dtype, int64_t m,
+                                   int64_t lda, const double* b, const double* x, double* g);
 
 /*
  * Allocation-free form of spcg_gram_apply: w = A^T (A p) in one read of A,

@@ -113,11 +113,18 @@ static spcg_status start_sequence(spcg_ctx* c, const PassGeom& g, const double* 
   return SPCG_OK;
 }
 
-// One PCG iteration (four launches) after start_sequence or a previous one;
-// the pass multiplies by the operand g (the FP32 copy of X in mixed mode).
-static spcg_status iteration(spcg_ctx* c, const PassGeom& g, double* beta, int& cur, int& pp,
+// Operand of the fused pass: one array (FP64, FP32 or BF16 rows), or the
+// double-FP32 pair Xh + Xl when tml is set.
+struct Operand {
+  const PassGeom* g;
+  const CUtensorMap* tml;
+};
+
+// One PCG iteration (four launches) after start_sequence or a previous one.
+static spcg_status iteration(spcg_ctx* c, const Operand& op, double* beta, int& cur, int& pp,
                              int& gp, int start, int check, double tau) {
-  SPCG_TRY(pass_gram_iter(c, g, pp, gp, start, check, tau));
+  if (op.tml) SPCG_TRY(pass_gram_iter_df(c, *op.g, *op.tml, pp, gp, start, check, tau));
+  else SPCG_TRY(pass_gram_iter(c, *op.g, pp, gp, start, check, tau));
   pp ^= 1;
   gp ^= 1;
   SPCG_TRY(launch_reduce(c, c->pb.w, c->pb.p[pp]));
@@ -132,7 +139,8 @@ static spcg_status run_stage(spcg_ctx* c, int i, int a_i, double* beta) {
   SPCG_TRY(launch_reset_flags(c));
   int cur = 0, pp = 0, gp = 0;
   SPCG_TRY(start_sequence(c, g, c->sk.bK + c->sk.stage_off[i], beta, cur));
-  for (int k = 0; k < a_i; ++k) SPCG_TRY(iteration(c, g, beta, cur, pp, gp, k == 0, 0, 0.0));
+  const Operand op{&g, nullptr};
+  for (int k = 0; k < a_i; ++k) SPCG_TRY(iteration(c, op, beta, cur, pp, gp, k == 0, 0, 0.0));
   return SPCG_OK;
 }
 
@@ -146,7 +154,8 @@ static spcg_status run_stage_m(spcg_ctx* c, int64_t m, int a_i, double* beta) {
   SPCG_TRY(launch_reset_flags(c));
   int cur = 0, pp = 0, gp = 0;
   SPCG_TRY(start_sequence(c, g, c->sk.bK, beta, cur));
-  for (int k = 0; k < a_i; ++k) SPCG_TRY(iteration(c, g, beta, cur, pp, gp, k == 0, 0, 0.0));
+  const Operand op{&g, nullptr};
+  for (int k = 0; k < a_i; ++k) SPCG_TRY(iteration(c, op, beta, cur, pp, gp, k == 0, 0, 0.0));
   return SPCG_OK;
 }
 
@@ -154,17 +163,49 @@ struct RefineResult {
   int iters = 0, restarts = 0, converged = 0;
 };
 
+// Stage II operand of the mixed path: FP32 rows while 2^-24 nu <= 1/32 (nu
+// the ||D R^{-1}||_2 estimate of the sketch), else the double-FP32 pair.
+constexpr double kInnerF32MaxPerturbation = 1.0 / 32.0;
+
+// True gradients of the mixed path: double-FP32 while 2^-48 nu <= tol/64.
+// The double-FP32 error per term is near 2^-48 relative; reaching the
+// stopping metric it is amplified by up to nu, and the test compares it with
+// (tol/2) ||R beta||.
+constexpr double kGradDfMaxPerturbationPerTol = 1.0 / 64.0;
+
+static int choose_grad(const spcg_ctx* c, double tol) {
+  if (c->opts.precision != SPCG_PREC_MIXED) return SPCG_GRAD_F64;
+  if (c->opts.grad_prec == SPCG_GRAD_F64 || c->opts.grad_prec == SPCG_GRAD_DF)
+    return c->opts.grad_prec;
+  return ldexp(c->cond_est, -48) <= kGradDfMaxPerturbationPerTol * tol ? SPCG_GRAD_DF
+                                                                       : SPCG_GRAD_F64;
+}
+
+static int choose_inner(const spcg_ctx* c) {
+  if (c->opts.inner_prec == SPCG_INNER_F32 || c->opts.inner_prec == SPCG_INNER_DF)
+    return c->opts.inner_prec;
+  return ldexp(c->cond_est, -24) <= kInnerF32MaxPerturbation ? SPCG_INNER_F32 : SPCG_INNER_DF;
+}
+
 static spcg_status run_refine(spcg_ctx* c, double tol, int max_iters, int max_restarts,
                               double* beta, RefineResult* res) {
   const double tau = tol / 2.0;
+  const bool mixed = c->opts.precision == SPCG_PREC_MIXED;
   const PassGeom& g = c->gx;                                  // true gradients: FP64 X
-  const PassGeom& gi = (c->opts.precision == SPCG_PREC_MIXED) ? c->gxf : c->gx;   // iterations
+  Operand gi{&c->gx, nullptr};                                // iterations
+  c->inner_used = 0;
+  c->grad_used = choose_grad(c, tol);
+  const bool df_grad = c->grad_used == SPCG_GRAD_DF;
+  if (mixed) {
+    c->inner_used = choose_inner(c);
+    gi = c->inner_used == SPCG_INNER_DF ? Operand{&c->gxdf, &c->tml} : Operand{&c->gxf, nullptr};
+  }
   int total = 0, restarts = 0;
   SPCG_TRY(launch_reset_flags(c));
   for (;;) {
     // true gradient and the stopping test on it
     int cur = 0, pp = 0, gp = 0;
-    SPCG_TRY(start_sequence(c, g, c->Y, beta, cur, c->opts.precision == SPCG_PREC_MIXED));
+    SPCG_TRY(start_sequence(c, g, c->Y, beta, cur, df_grad));
     SPCG_TRY(launch_check(c, tau));
     SPCG_TRY(sync_scalars(c));
     if (c->host_scal.done) {
@@ -482,7 +523,9 @@ extern "C" spcg_status spcg_sketch(spcg_ctx* c, uint64_t seed, const spcg_schedu
     SPCG_TRY(launch_transform(c));
   }
   SPCG_TRY(launch_precond_factor(c));
+  if (s.mixed) SPCG_TRY(launch_condest(c));
   SPCG_TRY(sync_scalars(c));
+  c->cond_est = s.mixed ? c->host_scal.cond : 0.0;
   s.ready = true;
   return SPCG_OK;
 }
@@ -541,6 +584,9 @@ extern "C" spcg_status spcg_solve(spcg_ctx* c, uint64_t seed, const spcg_schedul
     info->sqrt_gamma = c->host_scal.sqrt_gamma;
     info->norm_R_beta = c->host_scal.norm_rb;
     info->bytes_pass = c->pass_bytes;
+    info->cond_est = c->cond_est;
+    info->inner_prec = c->inner_used;
+    info->grad_prec = c->grad_used;
     float ms;
     cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
     info->ms_sketch = ms;
@@ -612,7 +658,7 @@ extern "C" spcg_status spcg_gram_apply(spcg_ctx* c, const double* A, int64_t m, 
 
 extern "C" spcg_status spcg_gram_apply_typed(spcg_ctx* c, const void* A, int32_t dtype, int64_t m,
                                              int64_t lda, const double* p, double* w) {
-  if (!c || !p || !w || m < 0 || dtype < 0 || dtype > 2) return SPCG_E_INVALID_ARG;
+  if (!c || !p || !w || m < 0 || dtype < 0 || dtype > 3) return SPCG_E_INVALID_ARG;
   if (m == 0) {
     SPCG_CK(cudaMemsetAsync(w, 0, (size_t)c->d * 8, c->stream));
     SPCG_CK(cudaStreamSynchronize(c->stream));
@@ -620,10 +666,44 @@ extern "C" spcg_status spcg_gram_apply_typed(spcg_ctx* c, const void* A, int32_t
   }
   if (!A) return SPCG_E_INVALID_ARG;
   PassGeom g;
-  SPCG_TRY(make_pass_geom_t(A, m, c->d, lda, dtype, &g));
   SPCG_TRY(launch_reset_flags(c));
-  SPCG_TRY(pass_gram_plain(c, g, p));
+  if (dtype == 3) {   // double-FP32 pair: hi block, then lo block
+    if (m > (int64_t(1) << 40) / (lda > 0 ? lda : 1)) return SPCG_E_INVALID_ARG;
+    const float* hi = static_cast<const float*>(A);
+    CUtensorMap tml;
+    SPCG_TRY(make_pass_geom_df(hi, hi + m * lda, m, c->d, lda, &g, &tml));
+    SPCG_TRY(pass_gram_plain_df(c, g, tml, p));
+  } else {
+    SPCG_TRY(make_pass_geom_t(A, m, c->d, lda, dtype, &g));
+    SPCG_TRY(pass_gram_plain(c, g, p));
+  }
   SPCG_TRY(launch_reduce(c, w, nullptr));
+  return sync_scalars(c);
+}
+
+extern "C" spcg_status spcg_resid_apply_typed(spcg_ctx* c, const void* A, int32_t dtype,
+                                              int64_t m, int64_t lda, const double* b,
+                                              const double* x, double* g) {
+  if (!c || !x || !g || m < 0 || dtype < 0 || dtype > 3) return SPCG_E_INVALID_ARG;
+  if (m == 0) {
+    SPCG_CK(cudaMemsetAsync(g, 0, (size_t)c->d * 8, c->stream));
+    SPCG_CK(cudaStreamSynchronize(c->stream));
+    return SPCG_OK;
+  }
+  if (!A || !b) return SPCG_E_INVALID_ARG;
+  PassGeom geo;
+  SPCG_TRY(launch_reset_flags(c));
+  if (dtype == 3) {
+    if (m > (int64_t(1) << 40) / (lda > 0 ? lda : 1)) return SPCG_E_INVALID_ARG;
+    const float* hi = static_cast<const float*>(A);
+    CUtensorMap tml;
+    SPCG_TRY(make_pass_geom_df(hi, hi + m * lda, m, c->d, lda, &geo, &tml));
+    SPCG_TRY(pass_resid_df(c, geo, tml, b, x));
+  } else {
+    SPCG_TRY(make_pass_geom_t(A, m, c->d, lda, dtype, &geo));
+    SPCG_TRY(pass_resid(c, geo, b, x));
+  }
+  SPCG_TRY(launch_reduce(c, g, nullptr));
   return sync_scalars(c);
 }
 
@@ -750,6 +830,9 @@ static spcg_status solve_choice(spcg_ctx* c, uint64_t seed, const uint16_t* Wb, 
     info->sqrt_gamma = c->host_scal.sqrt_gamma;
     info->norm_R_beta = c->host_scal.norm_rb;
     info->bytes_pass = c->pass_bytes;
+    info->cond_est = c->cond_est;
+    info->inner_prec = c->inner_used;
+    info->grad_prec = c->grad_used;
     info->pass_launches = (int32_t)c->n_pass;
     info->launches = (int32_t)c->n_launch;
     info->pass_ms = c->prof_ms;

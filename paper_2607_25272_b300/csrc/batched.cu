@@ -127,14 +127,16 @@ __device__ __forceinline__ double b_unfixed(long long q, int s) {
   return ldexp((double)q, -s);
 }
 
-// double-FP32 helpers (error-free transformations)
+// double-FP32 helpers (error-free transformations); the _rn intrinsics keep
+// the compiler from contracting a product and a sum into one FMA, which
+// would break the error terms
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = a * b;
+  p = __fmul_rn(a, b);
   e = fmaf(a, b, -p);
 }
 
@@ -253,7 +255,7 @@ __device__ bool stream_pass(BShared& sh, unsigned char* ring, size_t ring_bytes,
             float s2, se;
             two_sum(sh_, oh, s2, se);
             sh_ = s2;
-            sl += ol + se;
+            sl = __fadd_rn(__fadd_rn(sl, ol), se);   // same bits in both partner lanes
           }
           const float y = bvec32[r0 + rr];
           float th, tl;

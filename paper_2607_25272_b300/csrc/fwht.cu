@@ -430,21 +430,48 @@ spcg_status launch_export_rows(spcg_ctx* c, int64_t row0, int64_t n, double* A, 
 
 // The FP32 split X = Xh + Xl of the mixed-precision Stage II: the iterations
 // read Xh, the true gradients read both halves.
-__global__ void k_to_f32(const double* __restrict__ X, int64_t ldx, int64_t N, int d,
-                         float* __restrict__ Xf, float* __restrict__ Xl, int64_t ldxf) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * d;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / d;
-    const int j = (int)(e % d);
-    const double x = X[i * ldx + j];
-    const float h = __double2float_rn(x);
-    Xf[i * ldxf + j] = h;
-    Xl[i * ldxf + j] = __double2float_rn(x - (double)h);
+// Xh = fl32(X), Xl = fl32(X - Xh): one warp per row, 16-byte loads, four
+// loads in flight per lane before the stores.
+__global__ void __launch_bounds__(256) k_to_f32(const double* __restrict__ X, int64_t ldx,
+                                                int64_t N, int d, float* __restrict__ Xf,
+                                                float* __restrict__ Xl, int64_t ldxf) {
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31;
+  const int full = d / 2;   // complete column pairs
+  for (int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); i < N;
+       i += (int64_t)gridDim.x * 8) {
+    const double* xr = X + i * ldx;
+    float* hr = Xf + i * ldxf;
+    float* lr = Xl + i * ldxf;
+    for (int q0 = 0; q0 < full; q0 += 32 * U) {
+      double2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * 32 + lane;
+        if (q < full) v[u] = __ldcs(reinterpret_cast<const double2*>(xr) + q);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * 32 + lane;
+        if (q < full) {
+          const float h0 = __double2float_rn(v[u].x), h1 = __double2float_rn(v[u].y);
+          reinterpret_cast<float2*>(hr)[q] = make_float2(h0, h1);
+          reinterpret_cast<float2*>(lr)[q] = make_float2(__double2float_rn(v[u].x - (double)h0),
+                                                         __double2float_rn(v[u].y - (double)h1));
+        }
+      }
+    }
+    if ((d & 1) && lane == 0) {
+      const double x = xr[d - 1];
+      const float h = __double2float_rn(x);
+      hr[d - 1] = h;
+      lr[d - 1] = __double2float_rn(x - (double)h);
+    }
   }
 }
 
 spcg_status launch_to_f32(spcg_ctx* c) {
-  k_to_f32<<<4 * c->num_sms, 512, 0, c->stream>>>(c->X, c->ldx, c->N, c->d, c->Xf, c->Xl,
+  k_to_f32<<<8 * c->num_sms, 256, 0, c->stream>>>(c->X, c->ldx, c->N, c->d, c->Xf, c->Xl,
                                                    c->ldxf);
   SPCG_CK(cudaGetLastError());
   c->n_launch += 1;

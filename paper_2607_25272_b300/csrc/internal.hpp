@@ -17,6 +17,7 @@ struct DevScalars {
   double gam[2];     // gamma ping-pong
   double sqrt_gamma; // last check: sqrt(gamma)
   double norm_rb;    // last check: ||R beta||
+  double cond;       // estimate of ||D R^{-1}||_2 (condest.cu)
 };
 
 // Element types of a fused-pass operand.
@@ -119,6 +120,9 @@ struct spcg_ctx {
   double* feat_part = nullptr;   // feature partial sums
   int64_t ldxf = 0;
   spcg::PassGeom gxf{};          // pass geometry over Xf
+  double cond_est = 0.0;         // mixed path: ||D R^{-1}||_2 estimate of the last sketch
+  int inner_used = 0;            // mixed path: SPCG_INNER_* of the last Stage II
+  int grad_used = 0;             // SPCG_GRAD_* of the last Stage II
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // launch accounting and optional per-pass event timing
   int64_t n_launch = 0;
@@ -175,5 +179,11 @@ spcg_status make_pass_geom_df(const float* Xh, const float* Xl, int64_t m, int d
                               PassGeom* g, CUtensorMap* tml);
 spcg_status pass_resid_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml,
                           const double* b, const double* x);
+spcg_status pass_gram_plain_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml,
+                               const double* p);
+spcg_status pass_gram_iter_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml, int pp,
+                              int gp, int start, int check, double tau);
+// condest.cu
+spcg_status launch_condest(spcg_ctx* c);   // -> DevScalars::cond
 
 }  // namespace spcg

@@ -35,6 +35,8 @@ constexpr size_t kScalarBytes = 256;
 constexpr size_t kNoAllocScratchBytes =
     kScalarBytes + (size_t)kNoAllocMaxCtas * SPCG_MAX_D * sizeof(double);   // 1,310,976 B
 
+static_assert(sizeof(spcg::DevScalars) <= kScalarBytes, "scalar block outgrew its slot");
+
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;

@@ -114,11 +114,52 @@ __device__ __forceinline__ double warp_sum_array(const double* v, int n) {
   return warp_allsum(s);
 }
 
+// PASS_ITER prologue of both fused passes: gamma = g.z and ||R beta||^2 from
+// the previous launch's per-block partial dots, the breakdown and stopping
+// tests, and the CG ratio gamma / gamma_prev.  Called by every thread of the
+// CTA; false means the pass must not run (the caller returns before issuing a
+// copy).  The decision is uniform over the grid: every CTA reads the same
+// partials.
+__device__ bool iter_prologue(const PassArgs& a, double* s_scal, double& ratio) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {
+    const double gam = warp_sum_array(a.dots_gz, a.n_dots);
+    const double rb2 = warp_sum_array(a.dots_rb, a.n_dots);
+    if (lane == 0) {
+      s_scal[0] = gam;
+      s_scal[1] = sqrt(rb2);
+    }
+  }
+  __syncthreads();
+  const double gam = s_scal[0], rb = s_scal[1];
+  int flag = 0;
+  if (!isfinite(gam) || gam < 0.0) flag = 2;
+  else if (gam == 0.0 || (a.check && sqrt(gam) <= a.tau * rb)) flag = 1;
+  if (flag) {
+    if (blockIdx.x == 0 && tid == 0) {
+      if (flag == 2) atomicExch(&a.scal->status, DEV_BREAKDOWN);
+      else {
+        a.scal->done = 1;
+        a.scal->sqrt_gamma = sqrt(gam);
+        a.scal->norm_rb = rb;
+      }
+    }
+    return false;
+  }
+  ratio = a.start ? 0.0 : gam / a.scal->gam[a.gp];
+  if (blockIdx.x == 0 && tid == 0) {
+    a.scal->gam[a.gp ^ 1] = gam;
+    a.scal->iters += 1;
+  }
+  return true;
+}
+
 // Element types of the operand and the accumulation they use: FP64 rows
-// accumulate in FP64; FP32 rows (the refinement copy of X) in FP32 with
-// compensated products and sums (TwoProd by FMA, TwoSum; Ogita, Rump and
-// Oishi's Dot2), which carries about twice the FP32 precision; BF16 rows (the
-// sketched prefix of Stage I) in plain FP32.
+// accumulate in FP64; FP32 rows (the refinement copy of X) form t = a.p in
+// FP32 and add t a into FP32 block sums that are folded into a compensated
+// (TwoSum) accumulator every few tiles, so the long sums over rows keep about
+// twice the FP32 precision; BF16 rows (the sketched prefix of Stage I) use
+// plain FP32 throughout.
 template <typename T> struct PassElem;
 template <> struct PassElem<double> {
   using acc = double;
@@ -194,44 +235,19 @@ __global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
   }
 
   // ---- prologue: the direction this pass multiplies ----
-  if (a.mode == PASS_ITER) {
-    if (warp == 0) {
-      const double gam = warp_sum_array(a.dots_gz, a.n_dots);
-      const double rb2 = warp_sum_array(a.dots_rb, a.n_dots);
-      if (lane == 0) {
-        s_scal[0] = gam;
-        s_scal[1] = sqrt(rb2);
+  double ratio = 0.0;
+  if (a.mode == PASS_ITER && !iter_prologue(a, s_scal, ratio)) return;   // no TMA issued yet
+  for (int j = tid; j < RS; j += blockDim.x) {
+    double v = 0.0;
+    if (j < a.d) {
+      if (a.mode == PASS_ITER) {
+        v = a.z[j] + ratio * a.p_prev[j];
+        if (blockIdx.x == 0) a.p_next[j] = v;
+      } else {
+        v = a.vec[j];
       }
     }
-    __syncthreads();
-    const double gam = s_scal[0], rb = s_scal[1];
-    int flag = 0;
-    if (!isfinite(gam) || gam < 0.0) flag = 2;
-    else if (gam == 0.0 || (a.check && sqrt(gam) <= a.tau * rb)) flag = 1;
-    if (flag) {
-      if (blockIdx.x == 0 && tid == 0) {
-        if (flag == 2) atomicExch(&a.scal->status, DEV_BREAKDOWN);
-        else {
-          a.scal->done = 1;
-          a.scal->sqrt_gamma = sqrt(gam);
-          a.scal->norm_rb = rb;
-        }
-      }
-      return;   // no TMA issued yet
-    }
-    const double ratio = a.start ? 0.0 : gam / a.scal->gam[a.gp];
-    for (int j = tid; j < RS; j += blockDim.x) {
-      double v = 0.0;
-      if (j < a.d) v = a.z[j] + ratio * a.p_prev[j];
-      vec_s[j] = (acc_t)v;
-      if (blockIdx.x == 0 && j < a.d) a.p_next[j] = v;
-    }
-    if (blockIdx.x == 0 && tid == 0) {
-      a.scal->gam[a.gp ^ 1] = gam;
-      a.scal->iters += 1;
-    }
-  } else {
-    for (int j = tid; j < RS; j += blockDim.x) vec_s[j] = (acc_t)((j < a.d) ? a.vec[j] : 0.0);
+    vec_s[j] = (acc_t)v;
   }
   __syncthreads();
 
@@ -303,7 +319,11 @@ __global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
       const int tile = blockIdx.x + k * gridDim.x;
       const int64_t row0 = (int64_t)tile * a.tm;
       const T* st = tiles + (size_t)s * a.stage_elems;
-      for (int rr = cw; rr < a.tm; rr += RW * kConsumers) {
+      // row r of the CTA's row stream (tile k, row rr) belongs to consumer
+      // r mod C: every consumer stays busy when a tile has fewer rows than
+      // there are consumers (wide FP64 rows)
+      const int r0 = (int)(((int64_t)cw - (int64_t)k * a.tm) % kConsumers + kConsumers) % kConsumers;
+      for (int rr = r0; rr < a.tm; rr += RW * kConsumers) {
         if (row0 + rr >= a.m) break;
         const T* rowp[RW];
         bool live[RW];
@@ -905,33 +925,46 @@ spcg_status launch_features(spcg_ctx* c, const double* beta, float* dev_out2) {
 namespace spcg {
 
 // ---------------------------------------------------------------------------
-// The true gradient g = X^T (b - X beta) of the mixed-precision path from the
-// FP32 split X = Xh + Xl (|X - Xh - Xl| <= 2^-48 |X|), in double-FP32
-// arithmetic: products by TwoProd (FMA), sums by TwoSum, beta and b split
-// into FP32 pairs.  Every FP64 value of X is read as 8 bytes of FP32 pairs,
-// so the pass streams at memory speed instead of the FP64 pipe's rate, with
-// an error near 2^-44 relative instead of 2^-53 -- far below the 1e-6 target.
+// The fused pass over the FP32 split X = Xh + Xl (|X - Xh - Xl| <= 2^-48 |X|)
+// in double-FP32 arithmetic: products by TwoProd (FMA), sums by TwoSum, the
+// direction (or beta) and b split into FP32 pairs.  Every FP64 value of X is
+// read as 8 bytes of FP32 pairs, so the pass streams at memory speed instead
+// of the FP64 pipe's rate, with an error near 2^-44 relative instead of 2^-53.
+// The mixed path takes every trusted gradient X^T (Y - X beta) from it, and,
+// when the condition estimate says that FP32 rows would perturb the
+// preconditioned operator too much, the Stage II iterations as well.  Modes
+// as k_pass (PLAIN, ITER with the same fused prologue, RESID).
 // ---------------------------------------------------------------------------
+// The error-free transformations use the _rn intrinsics on purpose: they are
+// never contracted into an FMA.  A contraction such as s = fma(x, y, a) for
+// s = a + x*y would fold the product's rounding error into s while the error
+// term still adds it back, counting it twice and leaving FP32-level accuracy.
 __device__ __forceinline__ void ts(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 template <int NI>
-__global__ void __launch_bounds__(32 * 9, 1)
+__global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
     k_pass_df(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUtensorMap tml,
               const PassArgs a) {
-  constexpr int KC = 8;
+  constexpr int KC = PassCfg<NI>::C;
+  // lanes own runs of V = 4 consecutive columns (one float4 of each half)
+  constexpr int V = 4;
+  constexpr int NG = (NI * 32 + 32 * V - 1) / (32 * V);
+  constexpr int RS = NG * 32 * V;
+  constexpr bool XCACHE = NI <= 16;   // keep the row in registers between the two products
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base_addr = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((128u - (base_addr & 127u)) & 127u);
   float* tiles = reinterpret_cast<float*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.region_bytes);
   uint64_t* empty = full + kMaxStages;
-  float* bh_s = reinterpret_cast<float*>(empty + kMaxStages);
-  float* bl_s = bh_s + NI * 32;
+  float* vh_s = reinterpret_cast<float*>(empty + kMaxStages);
+  float* vl_s = vh_s + RS;
   __shared__ int s_abort;
+  __shared__ double s_scal[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (a.scal->status != 0 || a.scal->done != 0) return;
   if (tid == 0) {
@@ -943,17 +976,29 @@ __global__ void __launch_bounds__(32 * 9, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  for (int j = tid; j < NI * 32; j += blockDim.x) {
-    const double v = (j < a.d) ? a.vec[j] : 0.0;
+  double ratio = 0.0;
+  if (a.mode == PASS_ITER && !iter_prologue(a, s_scal, ratio)) return;
+  for (int j = tid; j < RS; j += blockDim.x) {
+    double v = 0.0;
+    if (j < a.d) {
+      if (a.mode == PASS_ITER) {
+        v = a.z[j] + ratio * a.p_prev[j];
+        if (blockIdx.x == 0) a.p_next[j] = v;
+      } else {
+        v = a.vec[j];
+      }
+    }
     const float h = (float)v;
-    bh_s[j] = h;
-    bl_s[j] = (float)(v - (double)h);
+    vh_s[j] = h;
+    vl_s[j] = (float)(v - (double)h);
   }
   __syncthreads();
   const int my_tiles = (blockIdx.x < a.ntiles) ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  float wacc[NI], wcmp[NI];
+  float wh[NG][V], wl[NG][V];   // w = sum of t x over this CTA's rows, as (sum, error)
 #pragma unroll
-  for (int i = 0; i < NI; ++i) wacc[i] = wcmp[i] = 0.f;
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int v = 0; v < V; ++v) wh[g][v] = wl[g][v] = 0.f;
   int issued = 0;
   if (warp == 0) {
     if (lane == 0) {
@@ -978,12 +1023,20 @@ __global__ void __launch_bounds__(32 * 9, 1)
     }
   } else {
     const int cw = warp - 1;
-    int off[NI];
+    int off[NG];
 #pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      const int c = lane + 32 * i;
-      off[i] = (c < a.d) ? (c / a.boxc) * (int)a.slot_elems + (c % a.boxc) : -1;
+    for (int g = 0; g < NG; ++g) {
+      const int c0 = g * 32 * V + lane * V;
+      off[g] = (c0 < a.d) ? (c0 / a.boxc) * (int)a.slot_elems + (c0 % a.boxc) : -1;
     }
+    float ph[NG][V], pl[NG][V];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        ph[g][v] = vh_s[g * 32 * V + lane * V + v];
+        pl[g][v] = vl_s[g * 32 * V + lane * V + v];
+      }
     const int lo_off = a.nbox * (int)a.slot_elems;
     for (int k = 0; k < my_tiles; ++k) {
       const int s = k % a.stages;
@@ -995,23 +1048,39 @@ __global__ void __launch_bounds__(32 * 9, 1)
       const int tile = blockIdx.x + k * gridDim.x;
       const int64_t row0 = (int64_t)tile * a.tm;
       const float* st = tiles + (size_t)s * a.stage_elems;
-      for (int rr = cw; rr < a.tm; rr += KC) {
+      const int r0 = (int)(((int64_t)cw - (int64_t)k * a.tm) % KC + KC) % KC;   // as in k_pass
+      for (int rr = r0; rr < a.tm; rr += KC) {
         if (row0 + rr >= a.m) break;
         const float* rh = st + rr * a.boxc;
         const float* rl = rh + lo_off;
-        float sh = 0.f, sl = 0.f;   // x . beta in double-FP32
+        float xh[XCACHE ? NG : 1][V], xl[XCACHE ? NG : 1][V];
+        float sh = 0.f, sl = 0.f;   // x . v in double-FP32
 #pragma unroll
-        for (int i = 0; i < NI; ++i) {
-          if (off[i] < 0) continue;
-          const float xh = rh[off[i]], xl = rl[off[i]];
-          const int c = lane + 32 * i;
-          const float p = xh * bh_s[c];
-          const float pe = fmaf(xh, bh_s[c], -p);
-          float s2, se;
-          ts(sh, p, s2, se);
-          sh = s2;
-          sl += pe + se + fmaf(xh, bl_s[c], xl * bh_s[c]);
+        for (int g = 0; g < NG; ++g) {
+          if (off[g] < 0) continue;
+          const float4 h4 = *reinterpret_cast<const float4*>(rh + off[g]);
+          const float4 l4 = *reinterpret_cast<const float4*>(rl + off[g]);
+          const float xa[V] = {h4.x, h4.y, h4.z, h4.w}, xb[V] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const float pr = __fmul_rn(xa[v], ph[g][v]);
+            const float pe = fmaf(xa[v], ph[g][v], -pr);
+            float s2, se;
+            ts(sh, pr, s2, se);
+            sh = s2;
+            sl += pe + se + fmaf(xa[v], pl[g][v], xb[v] * ph[g][v]);
+            if constexpr (XCACHE) {
+              xh[g][v] = xa[v];
+              xl[g][v] = xb[v];
+            }
+          }
         }
+        // Butterfly all-reduce of the pair.  Both partners must end with the
+        // same bits: sh + oh and sl + ol are commutative, and se is the exact
+        // error either way.  (sl += ol + se would round differently in the two
+        // lanes; with cancellation sl is not small against sh, and lanes would
+        // then scale their columns by slightly different t, an error that the
+        // stopping metric amplifies by ||D R^{-1}||.)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
@@ -1019,28 +1088,65 @@ __global__ void __launch_bounds__(32 * 9, 1)
           float s2, se;
           ts(sh, oh, s2, se);
           sh = s2;
-          sl += ol + se;
+          sl = __fadd_rn(__fadd_rn(sl, ol), se);
         }
-        // t = b - x . beta, as the pair (th, tl)
-        const double bv = a.b[row0 + rr];
-        const float b_h = (float)bv, b_l = (float)(bv - (double)b_h);
+        // t = x . v, or b - x . beta, as a normalised pair (th, tl)
         float th, tl;
-        ts(b_h, -sh, th, tl);
-        tl += b_l - sl;
-        const float t2 = th + tl;
-        tl = tl - (t2 - th);
-        th = t2;
-#pragma unroll
-        for (int i = 0; i < NI; ++i) {
-          if (off[i] < 0) continue;
-          const float xh = rh[off[i]], xl = rl[off[i]];
-          const float p = th * xh;
-          const float pe = fmaf(th, xh, -p);
-          float s2, se;
-          ts(wacc[i], p, s2, se);
-          wacc[i] = s2;
-          wcmp[i] += pe + se + fmaf(th, xl, tl * xh);
+        if (a.mode == PASS_RESID) {
+          const double bv = a.b[row0 + rr];
+          const float b_h = (float)bv, b_l = (float)(bv - (double)b_h);
+          ts(b_h, -sh, th, tl);
+          tl += b_l - sl;
+        } else {
+          th = sh;
+          tl = sl;
         }
+        {
+          float s2, se;
+          ts(th, tl, s2, se);
+          th = s2;
+          tl = se;
+        }
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          if (off[g] < 0) continue;
+          float xa[V], xb[V];
+          if constexpr (XCACHE) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              xa[v] = xh[g][v];
+              xb[v] = xl[g][v];
+            }
+          } else {
+            const float4 h4 = *reinterpret_cast<const float4*>(rh + off[g]);
+            const float4 l4 = *reinterpret_cast<const float4*>(rl + off[g]);
+            xa[0] = h4.x; xa[1] = h4.y; xa[2] = h4.z; xa[3] = h4.w;
+            xb[0] = l4.x; xb[1] = l4.y; xb[2] = l4.z; xb[3] = l4.w;
+          }
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const float pr = __fmul_rn(th, xa[v]);
+            const float pe = fmaf(th, xa[v], -pr);
+            float s2, se;
+            ts(wh[g][v], pr, s2, se);
+            wh[g][v] = s2;
+            wl[g][v] += pe + se + fmaf(th, xb[v], tl * xa[v]);
+          }
+        }
+      }
+      // Renormalise the pairs every few tiles: wl collects one TwoSum error
+      // per row and would otherwise grow with the rows a lane sums, and its
+      // own FP32 rounding with it.
+      if ((k & 7) == 7) {
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            float s2, se;
+            ts(wh[g][v], wl[g][v], s2, se);
+            wh[g][v] = s2;
+            wl[g][v] = se;
+          }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
@@ -1053,16 +1159,19 @@ __global__ void __launch_bounds__(32 * 9, 1)
       (void)mbar_wait_bounded(&full[k % a.stages], (k / a.stages) & 1, 1ll << 31);
   }
   __syncthreads();
-  double* red = reinterpret_cast<double*>(smem);
+  double* red = reinterpret_cast<double*>(smem);   // KC x RS, reuses the staging region
   if (warp > 0) {
 #pragma unroll
-    for (int i = 0; i < NI; ++i)
-      red[(warp - 1) * NI * 32 + lane + 32 * i] = (double)wacc[i] + (double)wcmp[i];
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        red[(size_t)(warp - 1) * RS + g * 32 * V + lane * V + v] =
+            (double)wh[g][v] + (double)wl[g][v];
   }
   __syncthreads();
   for (int j = tid; j < a.d; j += blockDim.x) {
     double sum = 0.0;
-    for (int w = 0; w < KC; ++w) sum += red[w * NI * 32 + j];
+    for (int w = 0; w < KC; ++w) sum += red[(size_t)w * RS + j];
     a.partials[(size_t)blockIdx.x * a.ldp + j] = sum;
   }
 }
@@ -1100,11 +1209,12 @@ spcg_status make_pass_geom_df(const float* Xh, const float* Xl, int64_t m, int d
   h.stages = stages;
   h.stage_bytes = stage;
   const size_t ni32 = (size_t)ni_for(d) * 32;
-  size_t red = (size_t)8 * ni32 * 8;
+  const size_t cover = ni32 > 256 ? ni32 : 256;   // RS of k_pass_df is at most this
+  size_t red = (size_t)kConsumers * cover * 8;
   size_t tiles = stage * stages;
   if (tiles < red) tiles = red;
   h.region_bytes = tiles;
-  h.smem_bytes = 128 + tiles + 2 * kMaxStages * 8 + 2 * ni32 * 4;
+  h.smem_bytes = 128 + tiles + 2 * kMaxStages * 8 + 2 * cover * 4;
   h.dtype = DT_F32;
   h.esize = 8;   // algorithmic bytes per element (the pair)
   *g = h;
@@ -1119,7 +1229,7 @@ static spcg_status launch_df_ni(spcg_ctx* c, const PassGeom& g, const CUtensorMa
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1));
   if (e0) SPCG_CK(cudaEventRecord(e0, c->stream));
-  k_pass_df<NI><<<grid, 32 * 9, g.smem_bytes, c->stream>>>(g.tmap, tml, a);
+  k_pass_df<NI><<<grid, PassCfg<NI>::THREADS, g.smem_bytes, c->stream>>>(g.tmap, tml, a);
   SPCG_CK(cudaGetLastError());
   if (e1) SPCG_CK(cudaEventRecord(e1, c->stream));
   c->n_launch += 1;
@@ -1128,15 +1238,11 @@ static spcg_status launch_df_ni(spcg_ctx* c, const PassGeom& g, const CUtensorMa
   return SPCG_OK;
 }
 
-spcg_status pass_resid_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml,
-                          const double* b, const double* x) {
+static spcg_status launch_pass_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml,
+                                  PassArgs a) {
   int grid = c->pb.grid;
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) grid = 1;
-  PassArgs a{};
-  a.mode = PASS_RESID;
-  a.vec = x;
-  a.b = b;
   a.m = g.m;
   a.d = g.d;
   a.nbox = g.nbox;
@@ -1162,6 +1268,40 @@ spcg_status pass_resid_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml
     case 32: return launch_df_ni<32>(c, g, tml, a, grid);
     default: return SPCG_E_INVALID_ARG;
   }
+}
+
+spcg_status pass_resid_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml,
+                          const double* b, const double* x) {
+  PassArgs a{};
+  a.mode = PASS_RESID;
+  a.vec = x;
+  a.b = b;
+  return launch_pass_df(c, g, tml, a);
+}
+
+spcg_status pass_gram_plain_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml,
+                               const double* p) {
+  PassArgs a{};
+  a.mode = PASS_PLAIN;
+  a.vec = p;
+  return launch_pass_df(c, g, tml, a);
+}
+
+spcg_status pass_gram_iter_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap& tml, int pp,
+                              int gp, int start, int check, double tau) {
+  PassArgs a{};
+  a.mode = PASS_ITER;
+  a.z = c->pb.z;
+  a.p_prev = c->pb.p[pp];
+  a.p_next = c->pb.p[pp ^ 1];
+  a.dots_gz = c->pb.dots_gz;
+  a.dots_rb = c->pb.dots_rb;
+  a.n_dots = c->pb.n_pre;
+  a.gp = gp;
+  a.start = start;
+  a.check = check;
+  a.tau = tau;
+  return launch_pass_df(c, g, tml, a);
 }
 
 }  // namespace spcg

@@ -41,6 +41,12 @@ SPCG_E_STATE = 7
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+INNER_AUTO = 0
+INNER_F32 = 1
+INNER_DF = 2
+GRAD_AUTO = 0
+GRAD_F64 = 1
+GRAD_DF = 2
 SKETCH_SRHT = 0
 SKETCH_COUNT = 1
 DTYPE_CODE = {"float64": 0, "float32": 1, "bfloat16": 2}
@@ -77,7 +83,8 @@ class Opts(ctypes.Structure):
         ("spin_budget", ctypes.c_int64),
         ("inject_stall", ctypes.c_int32),
         ("profile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("inner_prec", ctypes.c_int32),
+        ("grad_prec", ctypes.c_int32),
     ]
 
 
@@ -97,6 +104,9 @@ class Info(ctypes.Structure):
         ("pass_launches", ctypes.c_int32),
         ("launches", ctypes.c_int32),
         ("pass_ms", ctypes.c_double),
+        ("cond_est", ctypes.c_double),
+        ("inner_prec", ctypes.c_int32),
+        ("grad_prec", ctypes.c_int32),
     ]
 
 
@@ -136,6 +146,8 @@ _SIGS = {
     "spcg_gram_apply": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
     "spcg_gram_apply_typed": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                              _P, _P]),
+    "spcg_resid_apply_typed": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64,
+                                              ctypes.c_int64, _P, _P, _P]),
     "spcg_batch_create": (ctypes.c_int, [ctypes.POINTER(ProblemF32), ctypes.c_int32, _P,
                                          ctypes.POINTER(_P)]),
     "spcg_batch_destroy": (None, [_P]),
@@ -384,6 +396,34 @@ class Solver:
                                          _ptr(p), _ptr(w))
         _check(st, "spcg_gram_apply_typed")
         return w
+
+    def gram_apply_pair(self, AhAl, m, lda, p, w=None):
+        """w = A^T (A p) for the double-FP32 pair A = Ah + Al.
+
+        AhAl: CUDA float32 tensor holding Ah (m x lda) and then Al (m x lda)
+        contiguously; the first d columns of each row are used."""
+        import torch
+        if w is None:
+            w = torch.empty(self.d, dtype=torch.float64, device=p.device)
+        st = lib().spcg_gram_apply_typed(self.ctx, _ptr(AhAl) if m > 0 else None, 3, m, lda,
+                                         _ptr(p), _ptr(w))
+        _check(st, "spcg_gram_apply_typed")
+        return w
+
+    def resid_apply(self, A, b, x, g=None, dtype=None, m=None, lda=None):
+        """g = A^T (b - A x); A a row-major CUDA tensor (FP64/FP32/BF16), or
+        with dtype=3 the hi-then-lo FP32 pair buffer of gram_apply_pair."""
+        import torch
+        if g is None:
+            g = torch.empty(self.d, dtype=torch.float64, device=x.device)
+        if dtype is None:
+            dtype = DTYPE_CODE[str(A.dtype).replace("torch.", "")]
+            m = A.shape[0]
+            lda = A.stride(0) if m > 0 else self.d
+        st = lib().spcg_resid_apply_typed(self.ctx, _ptr(A) if m > 0 else None, dtype, m, lda,
+                                          _ptr(b) if m > 0 else None, _ptr(x), _ptr(g))
+        _check(st, "spcg_resid_apply_typed")
+        return g
 
     def gram_apply(self, A, p, w=None):
         import torch

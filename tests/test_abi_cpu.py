@@ -2,6 +2,7 @@
 include/spcg.h declares, and its host-only entry points (no CUDA call)
 agree with the oracle's schedule reading of Sec. 4."""
 import ctypes
+import os
 
 import pytest
 
@@ -69,3 +70,33 @@ def test_struct_layouts_match_header_sizes():
     # spcg_schedule: int32 K, int64 m[40], int32 a[40], int64 r, double tol, 2 x int32
     assert ctypes.sizeof(S.Schedule) == 8 + 8 * 40 + 4 * 40 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(S.Opts) == 4 + 4 + 8 + 16
+
+
+def test_struct_layouts_match_a_c_compiler(tmp_path):
+    """sizeof and field offsets as gcc lays out the structs of include/spcg.h."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"spcg_schedule": S.Schedule, "spcg_opts": S.Opts, "spcg_info": S.Info,
+               "spcg_problem_f32": S.ProblemF32}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "spcg.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

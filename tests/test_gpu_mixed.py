@@ -134,3 +134,89 @@ def test_mixed_c2_full_size():
     assert st == S.SPCG_OK
     assert rel_pred_error(X, beta.cpu().numpy(), bh) <= 1e-6
     s.close()
+
+
+def _split_pair(A):
+    """A (float64) -> (Ah, Al) FP32 with Ah = fl32(A), Al = fl32(A - Ah)."""
+    Ah = A.astype(np.float32)
+    Al = (A - Ah.astype(np.float64)).astype(np.float32)
+    return Ah, Al
+
+
+@pytest.mark.parametrize("m,d", [(1, 1), (1000, 33), (4097, 256), (3001, 257), (100003, 50),
+                                 (20000, 500), (513, 1000)])
+def test_pair_pass_parity(m, d):
+    """Double-FP32 pass against FP64 on the same pair: products are exact
+    (TwoProd) but for the dropped Al*pl term and the FP32 cross terms, both
+    near 2^-48 relative; sums are TwoSum-compensated.  Bound: 2^-40 of the
+    magnitude sum, a margin of 2^8 over that analysis, still 2^16 below the
+    FP32 pass's error."""
+    rng = np.random.default_rng(7 * m + d)
+    A = rng.standard_normal((m, d)) * np.exp(rng.uniform(-3, 3, size=d))[None, :]
+    p = rng.standard_normal(d)
+    Ah, Al = _split_pair(A)
+    ld = (d + 3) // 4 * 4
+    buf = torch.zeros(2 * m * ld, dtype=torch.float32, device="cuda")
+    v = buf.view(2, m, ld)
+    v[0, :, :d] = cuda(Ah)
+    v[1, :, :d] = cuda(Al)
+    s = S.Solver(cuda(rng.standard_normal((d + 2, d))), cuda(np.zeros(d + 2)))
+    w = s.gram_apply_pair(buf, m, ld, cuda(p)).cpu().numpy()
+    s.close()
+    Apair = Ah.astype(np.float64) + Al.astype(np.float64)
+    ref = Apair.T @ (Apair @ p)
+    mag = np.abs(Apair).T @ (np.abs(Apair) @ np.abs(p))
+    assert np.all(np.abs(w - ref) <= 2.0 ** -40 * mag + 1e-300)
+
+
+def _exact_nu(R):
+    D = np.sqrt((R * R).sum(axis=0))
+    return np.linalg.norm(D[:, None] * np.linalg.inv(R), 2)
+
+
+@pytest.mark.parametrize("N,d,kappa,seed", [(20000, 50, 1e4, 1), (30000, 200, 1e8, 2),
+                                            (16384, 40, 1e2, 3)])
+def test_condition_estimate_brackets_exact_norm(N, d, kappa, seed):
+    """cond_est is a power-iteration lower bound of ||D R^{-1}||_2."""
+    X, Y, _ = svd_problem(N, d, kappa, 0.1, seed=seed)
+    s = S.Solver(cuda(X), cuda(Y), mixed_opts())
+    sc = S.spcg_default_schedule(N, d)
+    beta, info, st = s.solve(seed, sc, raise_on_error=False)
+    R = s.export_precond()[0].cpu().numpy()
+    s.close()
+    nu = _exact_nu(R)
+    assert 0.3 * nu <= info.cond_est <= nu * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("inner", [0, 2])
+def test_mixed_kappa_1e8_converges(inner):
+    """At kappa = 1e8 the FP32 copy of X perturbs the preconditioned operator
+    by about 2^-24 nu > 1; the automatic rule must take the double-FP32 pair
+    and still meet 1e-6 against the oracle's OLS estimator."""
+    N, d, seed = 65536, 200, 4
+    X, Y, _ = svd_problem(N, d, 1e8, 1.0, seed=seed, leverage_df=3)
+    bh = OL.ols(X, Y)
+    o = mixed_opts()
+    o.inner_prec = inner
+    s = S.Solver(cuda(X), cuda(Y), o)
+    sc = S.spcg_default_schedule(N, d)
+    beta, info, st = s.solve(seed, sc, raise_on_error=False)
+    s.close()
+    assert info.cond_est * 2.0 ** -24 > 1.0 / 32
+    assert info.inner_prec == S.INNER_DF
+    # 2^-48 nu > tol / 64: the stopping rule must see FP64 true gradients
+    assert info.grad_prec == S.GRAD_F64
+    assert st == S.SPCG_OK and info.converged == 1
+    assert rel_pred_error(X, beta.cpu().numpy(), bh) <= 1e-6
+
+
+def test_auto_rule_keeps_fp32_when_well_conditioned():
+    N, d, seed = 16384, 40, 2
+    X, Y, _ = svd_problem(N, d, 1e3, 0.1, seed=seed)
+    s = S.Solver(cuda(X), cuda(Y), mixed_opts())
+    beta, info, st = s.solve(seed, S.spcg_default_schedule(N, d))
+    s.close()
+    assert st == S.SPCG_OK
+    assert info.cond_est * 2.0 ** -24 <= 1.0 / 32
+    assert info.inner_prec == S.INNER_F32
+    assert info.grad_prec == S.GRAD_DF
