@@ -44,8 +44,11 @@ WORKLOADS = {
                N=20000, d=50, kappa=None, sigma=1.0, seed=1, tol=1e-6),
 }
 CPU_SAMPLE_ROWS = 1 << 17     # oracle row sample for the CPU baseline
-# ncu: k_pass (FP64) on 262144 x 500 read 1.048667 GB + wrote 3.14 MB for 1.048576 GB of rows
-K_PASS_TRAFFIC_RATIO = (1.048667e9 + 3.142912e6) / 1.048576e9
+# DRAM bytes per algorithmic byte of k_pass (FP64) from one ncu capture of the
+# current kernel on a 262144 x 500 operand (profiles/k_pass_fp64_gram_262144x500.md):
+# read 1.048628 GB + wrote 3.604992 MB for 1.048576 GB of rows.  Set to None
+# whenever the kernel changes after the capture.
+K_PASS_TRAFFIC_RATIO = (1.048628e9 + 3.604992e6) / 1.048576e9
 
 
 def make_problem(w, N=None, seed_offset=0):
@@ -79,24 +82,37 @@ def time_solves(solver, seed, sched, steps, warmup, stream, fn=None):
     return e0.elapsed_time(e1) / steps, outs
 
 
+def closed_form_rel_error(beta, uty, s, V):
+    """||X (beta - beta_ols)|| / ||X beta_ols|| for X = U diag(s) V^T with U
+    orthonormal: beta_ols = V diag(1/s) U^T Y and ||X v|| = ||diag(s) V^T v||,
+    exact up to the orthonormality of U (CholeskyQR2, near 1e-15)."""
+    import torch
+    b_ols = V @ (uty / s)
+    return float(torch.linalg.norm(s * (V.T @ (beta - b_ols))) /
+                 torch.linalg.norm(s * (V.T @ b_ols)))
+
+
 def run_forms(args, w):
-    """Plain FP64 vs mixed precision on one large problem (C3)."""
+    """Plain FP64 vs mixed precision on one large problem (C3).  The problem
+    is drawn on the GPU (host generation of 4M x 1000 takes minutes); the
+    prediction error against the OLS estimator comes from the construction's
+    closed form (closed_form_rel_error)."""
     import torch
 
-    from oracle.linalg import ols_lowmem
-    from oracle.metrics import rel_pred_error
     from paper_2607_25272_b300 import spcg as S
-    t0 = time.time()
-    X, Y, _ = make_problem(w)
-    gen_s = time.time() - t0
-    N, d = X.shape
+    from paper_2607_25272_b300.inputs import svd_problem_device
     dev = torch.device("cuda", 0)
+    t0 = time.time()
+    Xd, Yd, _, uty, sv_s, sv_V = svd_problem_device(w["N"], w["d"], w["kappa"], w["sigma"],
+                                                    seed=w["seed"],
+                                                    leverage_df=w.get("leverage_df"),
+                                                    device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    N, d = Xd.shape
     stream = torch.cuda.current_stream(dev)
-    Xd = torch.from_numpy(X).to(dev)
-    Yd = torch.from_numpy(Y).to(dev)
     sched = S.spcg_default_schedule(N, d)
     sched.tol = w["tol"]
-    sched.max_restarts = 20
     res = {}
     for name, prec in (("plain_fp64", S.PREC_FP64), ("mixed", S.PREC_MIXED)):
         o = S.Opts()
@@ -109,25 +125,27 @@ def run_forms(args, w):
         pv = S.Solver(Xd, Yd, o)
         _, pinfo, _ = pv.solve(w["seed"], sched, raise_on_error=False)
         pv.close()
-        res[name] = {"s": ms / 1e3, "status": S.STATUS[st], "beta": beta.cpu().numpy(),
+        res[name] = {"s": ms / 1e3, "status": S.STATUS[st],
+                     "rel_pred_error": closed_form_rel_error(beta, uty, sv_s, sv_V),
                      "phases_ms": {"sketch": info.ms_sketch, "stages": info.ms_stages,
                                    "refine": info.ms_refine},
                      "refine_iters": info.refine_iters, "restarts": info.restarts,
+                     "cond_est": info.cond_est, "inner_prec": info.inner_prec,
+                     "grad_prec": info.grad_prec, "launches": info.launches,
                      "pass_gbs": pinfo.bytes_pass / (pinfo.pass_ms / 1e3) / 1e9
                      if pinfo.pass_ms > 0 else None}
         sv.close()
-    t1 = time.time()
-    bh = ols_lowmem(X, Y)
-    ols_s = time.time() - t1
-    for name in res:
-        res[name]["rel_pred_error"] = rel_pred_error(X, res[name].pop("beta"), bh)
     line = base_line(args, w, res["mixed"]["s"],
                      "seconds to 1e-6 OLS prediction error (mixed precision vs plain FP64 SPCG)",
                      "bf16/f32/f64")
-    line["config"].update({"N": N, "d": d, "tol": w["tol"]})
+    line["config"].update({"N": N, "d": d, "tol": w["tol"],
+                           "inputs": "drawn on the GPU (svd_problem_device), same recipe",
+                           "l2": "no flush: X is 33.6 GB, larger than the 126 MB L2"})
     line["forms"] = res
     line["speedup_mixed_vs_plain_fp64"] = res["plain_fp64"]["s"] / res["mixed"]["s"]
-    line["host_s"] = {"generate": gen_s, "oracle_ols": ols_s}
+    line["accuracy_reference"] = ("closed-form OLS estimator of the construction, "
+                                  "V diag(1/s) U^T Y")
+    line["host_s"] = {"generate": gen_s}
     print(json.dumps(line), flush=True)
 
 
@@ -371,19 +389,32 @@ def run_pass_only(args, w, local_rank):
     g = torch.Generator(device=dev)
     g.manual_seed(1)
     m, d = args.rows, w["d"]
-    dt = getattr(torch, args.pass_dtype)
+    pair = args.pass_dtype == "pair"
+    dt = torch.float32 if pair else getattr(torch, args.pass_dtype)
     align = 16 // torch.empty(0, dtype=dt).element_size()     # rows 16-byte aligned (TMA)
     ld = (d + align - 1) // align * align
-    A = torch.zeros((m, ld), dtype=dt, device=dev)
-    A[:, :d] = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g).to(dt)
-    A = A[:, :d]
+    if pair:   # hi block then lo block of a double-FP32 split
+        X64 = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g)
+        A = torch.zeros(2 * m * ld, dtype=dt, device=dev)
+        v = A.view(2, m, ld)
+        v[0, :, :d] = X64.float()
+        v[1, :, :d] = (X64 - v[0, :, :d].double()).float()
+        del X64
+    else:
+        A = torch.zeros((m, ld), dtype=dt, device=dev)
+        A[:, :d] = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g).to(dt)
+        A = A[:, :d]
     p = torch.randn(d, dtype=torch.float64, device=dev, generator=g)
     opts = S.Opts()
     opts.profile = 1
     s = S.Solver(torch.randn((d + 2, d), dtype=torch.float64, device=dev, generator=g),
                  torch.zeros(d + 2, dtype=torch.float64, device=dev))
     out = torch.empty(d, dtype=torch.float64, device=dev)
-    call = s.gram_apply if args.pass_dtype == "float64" else s.gram_apply_typed
+    if pair:
+        def call(A, p, out):
+            return s.gram_apply_pair(A, m, ld, p, out)
+    else:
+        call = s.gram_apply if args.pass_dtype == "float64" else s.gram_apply_typed
     for _ in range(args.warmup):
         call(A, p, out)
     stream = torch.cuda.current_stream(dev)
@@ -396,8 +427,9 @@ def run_pass_only(args, w, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    nbytes = m * d * A.element_size()
-    print(json.dumps({"kernel": f"k_pass<{args.pass_dtype}> via spcg_gram_apply (pass + reduce + sync)",
+    nbytes = m * d * (8 if pair else A.element_size())
+    kname = "k_pass_df (double-FP32 pair)" if pair else f"k_pass<{args.pass_dtype}>"
+    print(json.dumps({"kernel": f"{kname} via spcg_gram_apply (pass + reduce + sync)",
                       "rows": m, "d": d, "ms_per_call": ms, "alg_bytes": nbytes,
                       "gbs": nbytes / ms / 1e6, "tflops": 4 * m * d / ms / 1e9}), flush=True)
     s.close()
@@ -468,6 +500,8 @@ def run_ours(args, w, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         barrier()
         torch.cuda.synchronize()
+        if args.ncu_region == "plain":
+            torch.cuda.profiler.start()
         e0.record(stream)
         for _ in range(args.steps):
             _, info, st = solver.solve(w["seed"], sched, beta)
@@ -475,6 +509,8 @@ def run_ours(args, w, rank, world, local_rank):
             infos.append(info)
         e1.record(stream)
         torch.cuda.synchronize()
+        if args.ncu_region == "plain":
+            torch.cuda.profiler.stop()
         barrier()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     beta_h = beta.cpu().numpy()
@@ -488,6 +524,8 @@ def run_ours(args, w, rank, world, local_rank):
     for _ in range(args.warmup):
         msolver.solve(w["seed"], sched, mbeta)
     torch.cuda.synchronize()
+    if args.ncu_region == "mixed":
+        torch.cuda.profiler.start()
     e0.record(stream)
     minfos = []
     for _ in range(args.steps):
@@ -495,6 +533,8 @@ def run_ours(args, w, rank, world, local_rank):
         minfos.append(minfo)
     e1.record(stream)
     torch.cuda.synchronize()
+    if args.ncu_region == "mixed":
+        torch.cuda.profiler.stop()
     ms_mixed = e0.elapsed_time(e1) / args.steps
     mbeta_h = mbeta.cpu().numpy()
     mopts.profile = 1
@@ -558,8 +598,8 @@ def run_ours(args, w, rank, world, local_rank):
                 "peak_source": "nominal B300 FP64 1.25 TFLOP/s (recipe table); FP64 FMA probe "
                                "measured 1.13 TFLOP/s",
                 # DRAM read+write bytes per launch from the ncu capture of this kernel on a
-                # 262144 x 500 operand (profiles/k_pass_fp64_gram_262144x500.md), scaled by
-                # rows to the average launch of the solve; None once the kernel changes.
+                # 262144 x 500 operand, scaled by rows to the average launch of the solve
+                # (traffic grows with the rows read); None once the kernel changes.
                 "traffic": bytes_per_launch * K_PASS_TRAFFIC_RATIO if K_PASS_TRAFFIC_RATIO else None,
                 "hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm_gbs / hbm_peak,
                 "hbm_peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
@@ -590,6 +630,8 @@ def run_ours(args, w, rank, world, local_rank):
                       "phases_ms": {"sketch": minfos[-1].ms_sketch, "stages": minfos[-1].ms_stages,
                                     "refine": minfos[-1].ms_refine},
                       "refine_iters": minfos[-1].refine_iters, "restarts": minfos[-1].restarts,
+                      "cond_est": minfos[-1].cond_est, "inner_prec": minfos[-1].inner_prec,
+                      "grad_prec": minfos[-1].grad_prec,
                       "pass_gbs": (mpinfo.bytes_pass / (mpinfo.pass_ms / 1e3) / 1e9)
                       if mpinfo.pass_ms > 0 else None,
                       "pass_hbm_frac": (mpinfo.bytes_pass / (mpinfo.pass_ms / 1e3) / 1e9
@@ -618,7 +660,11 @@ def main():
                     help="time one kernel alone instead of the solve")
     ap.add_argument("--rows", type=int, default=1 << 18)
     ap.add_argument("--weights", default=None, help="schedule model weights (npz) for c5")
-    ap.add_argument("--pass-dtype", default="float64", choices=["float64", "float32", "bfloat16"])
+    ap.add_argument("--ncu-region", default=None, choices=[None, "plain", "mixed"],
+                    help="bracket the timed solves of this form with cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
+    ap.add_argument("--pass-dtype", default="float64",
+                    choices=["float64", "float32", "bfloat16", "pair"])
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))

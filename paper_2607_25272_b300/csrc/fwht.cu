@@ -471,8 +471,15 @@ __global__ void __launch_bounds__(256) k_to_f32(const double* __restrict__ X, in
 }
 
 spcg_status launch_to_f32(spcg_ctx* c) {
-  k_to_f32<<<8 * c->num_sms, 256, 0, c->stream>>>(c->X, c->ldx, c->N, c->d, c->Xf, c->Xl,
-                                                   c->ldxf);
+  // one wave of resident CTAs: the grid-stride loop then has no tail wave
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int v = 0;
+    SPCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_to_f32, 256, 0));
+    per_sm = v > 0 ? v : 1;
+  }
+  k_to_f32<<<per_sm * c->num_sms, 256, 0, c->stream>>>(c->X, c->ldx, c->N, c->d, c->Xf, c->Xl,
+                                                        c->ldxf);
   SPCG_CK(cudaGetLastError());
   c->n_launch += 1;
   return SPCG_OK;

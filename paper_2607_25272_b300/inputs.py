@@ -77,3 +77,36 @@ def scaled_columns_problem(N, d, lo, hi, sigma, seed=1):
     beta = rng.standard_normal(d)
     zeta = sigma * rng.standard_normal(N)
     return X, _response(X, beta, zeta), beta
+
+
+def svd_problem_device(N, d, kappa, sigma, seed=1, leverage_df=None, device="cuda"):
+    """The svd_problem recipe drawn on a CUDA device with torch (for sizes
+    whose host generation takes minutes).  Same construction, a different
+    random stream: G iid N(0,1) (rows optionally scaled by |Student-t(df)|,
+    drawn as z / sqrt(chi2_df / df)), U = CholeskyQR2(G), V from the QR of a
+    Gaussian d x d matrix, s geometric from 1 to 1/kappa, X = U diag(s) V^T,
+    beta iid N(0,1), Y = X beta + sigma zeta.
+
+    Returns (X, Y, beta, U^T Y, s, V) as FP64 device tensors; U itself is
+    not kept (N x d), but U^T Y, s and V are what a caller needs to form the
+    OLS estimator of this construction in closed form."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = torch.float64
+    G = torch.randn((N, d), dtype=f64, device=device, generator=g)
+    if leverage_df is not None:
+        z = torch.randn(N, dtype=f64, device=device, generator=g)
+        chi = (torch.randn((N, int(leverage_df)), dtype=f64, device=device, generator=g) ** 2).sum(1)
+        G *= (z / torch.sqrt(chi / leverage_df)).abs()[:, None]
+    for _ in range(2):
+        L = torch.linalg.cholesky(G.T @ G)
+        G = torch.linalg.solve_triangular(L, G.T, upper=False).T.contiguous()
+    V, _ = torch.linalg.qr(torch.randn((d, d), dtype=f64, device=device, generator=g))
+    s = float(kappa) ** (-torch.arange(d, dtype=f64, device=device) / max(d - 1, 1))
+    X = (G * s[None, :]) @ V.T
+    beta = torch.randn(d, dtype=f64, device=device, generator=g)
+    Y = X @ beta + sigma * torch.randn(N, dtype=f64, device=device, generator=g)
+    uty = G.T @ Y
+    del G
+    return X.contiguous(), Y, beta, uty, s, V
