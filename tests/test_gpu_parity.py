@@ -133,14 +133,20 @@ def _oracle_sketch(X, Y, seed, sched):
     return ZX, ZY, stages, A_hat
 
 
-@pytest.mark.parametrize("N,d,seed", [(20000, 50, 1), (3000, 37, 5), (4097, 20, 9), (600, 20, 2),
-                                      (9000, 300, 4)])
-def test_sketch_rows_and_preconditioner(N, d, seed):
+# Besides the default r = 6d: preconditioner sketches of 12800 and 13000 rows.
+@pytest.mark.parametrize("N,d,seed,r", [(20000, 50, 1, None), (3000, 37, 5, None),
+                                        (4097, 20, 9, None), (600, 20, 2, None),
+                                        (9000, 300, 4, None), (40000, 70, 6, 12800),
+                                        (40000, 70, 7, 13000), (5000, 161, 8, None)])
+def test_sketch_rows_and_preconditioner(N, d, seed, r):
     X, Y, _ = gaussian_problem(N, d, 1.0, seed=seed)
     sched = OS.default_schedule(N, d)
+    if r is not None:
+        sched["r"] = r
     sched["r"] = min(sched["r"], sched["n_pad"])
     s = S.Solver(cuda(X), cuda(Y))
     sc = S.spcg_default_schedule(N, d)
+    sc.r = sched["r"]
     s.sketch(seed, sc)
     n_pad = sched["n_pad"]
     ZX, ZY, stages, A_hat = _oracle_sketch(X, Y, seed, sched)
