@@ -602,7 +602,9 @@ def run_ours(args, w, rank, world, local_rank):
                 # (traffic grows with the rows read); None once the kernel changes.
                 "traffic": bytes_per_launch * K_PASS_TRAFFIC_RATIO if K_PASS_TRAFFIC_RATIO else None,
                 "hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm_gbs / hbm_peak,
-                "hbm_peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
+                "hbm_peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs)"
+                                    if "hbm_gbs" in peaks else
+                                    "of fallback (6.4 TB/s, no MEASURED_PEAKS.json on this host)"),
                 "pass_launches_per_step": pass_n / args.steps,
                 "alg_bytes_per_launch": bytes_per_launch}
     cpu = None if args.no_cpu_baseline else cpu_baseline(w, steps=1)

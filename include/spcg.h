@@ -333,6 +333,18 @@ spcg_status spcg_resid_apply_typed(spcg_ctx* ctx, const void* A, int32_t dtype, 
                                    int64_t lda, const double* b, const double* x, double* g);
 
 /*
+ * The double-FP32 split the mixed form streams: Xh = fl32(X) and
+ * Xl = fl32(X - Xh), both rounded to nearest even, so |X - Xh - Xl| <= 2^-48 |X|
+ * for |X| in [2^-74, 2^127).  X: device N x d FP64, row-major, leading
+ * dimension ldx (even, X 16-byte aligned); Xh, Xl: device N x d FP32 outputs
+ * with leading dimension ldxf (even, 8-byte aligned), columns d.. untouched.
+ * Runs on `stream` and synchronises it.  SPCG_E_INVALID_ARG on a bad size,
+ * stride or alignment; N = 0 does nothing.
+ */
+spcg_status spcg_split_f32(const double* X, int64_t N, int32_t d, int64_t ldx, float* Xh,
+                           float* Xl, int64_t ldxf, void* stream);
+
+/*
  * Allocation-free form of spcg_gram_apply: w = A^T (A p) in one read of A,
  * with no context and no device allocation of any kind.  (The paper has no
  * counterpart; this entry point serves callers that cannot allocate device

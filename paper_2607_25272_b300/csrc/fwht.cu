@@ -430,8 +430,37 @@ spcg_status launch_export_rows(spcg_ctx* c, int64_t row0, int64_t n, double* A, 
 
 // The FP32 split X = Xh + Xl of the mixed-precision Stage II: the iterations
 // read Xh, the true gradients read both halves.
-// Xh = fl32(X), Xl = fl32(X - Xh): one warp per row, 16-byte loads, four
-// loads in flight per lane before the stores.
+// Xh = fl32(x) and Xl = fl32(x - Xh), round to nearest even, from the bit
+// pattern of x with integer and FP32 operations: this GPU's FP64 pipe (and
+// the double conversions) run at a small fraction of its integer and FP32
+// rates.  The float image keeps the top 24 significant bits; the 29 dropped
+// bits decide the rounding and, minus 2^29 when it rounded up, are the
+// remainder x - Xh in units of 2^(e-52): an integer below 2^29 in magnitude,
+// rounded once to FP32 and scaled exactly by a power of two.  Values outside
+// 2^-74 <= |x| < 2^127 (zero, subnormal, huge, Inf, NaN) take the
+// conversion instructions.
+__device__ __forceinline__ void split_f32(double x, float& h, float& l) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -74 || e > 126) {
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+    return;
+  }
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const unsigned long long frac = b & 0xFFFFFFFFFFFFFull;   // 52 fraction bits
+  const unsigned dropped = (unsigned)(frac & 0x1FFFFFFFull);  // the low 29 bits
+  unsigned mag = ((unsigned)(e + 127) << 23) | (unsigned)(frac >> 29);
+  const bool up = dropped > 0x10000000u || (dropped == 0x10000000u && (mag & 1u));
+  mag += up ? 1u : 0u;   // a carry into the exponent field is the correct rounding
+  h = __uint_as_float(sign | mag);
+  const int rem = (int)dropped - (up ? (1 << 29) : 0);
+  const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);   // 2^(e-52), normal
+  l = (float)(sign ? -rem : rem) * scale;   // an exact zero stays +0, as x - Xh does
+}
+
+// Xh, Xl for an N x d block: one warp per row, 16-byte loads, four loads in
+// flight per lane before the stores.
 __global__ void __launch_bounds__(256) k_to_f32(const double* __restrict__ X, int64_t ldx,
                                                 int64_t N, int d, float* __restrict__ Xf,
                                                 float* __restrict__ Xl, int64_t ldxf) {
@@ -454,35 +483,57 @@ __global__ void __launch_bounds__(256) k_to_f32(const double* __restrict__ X, in
       for (int u = 0; u < U; ++u) {
         const int q = q0 + u * 32 + lane;
         if (q < full) {
-          const float h0 = __double2float_rn(v[u].x), h1 = __double2float_rn(v[u].y);
+          float h0, l0, h1, l1;
+          split_f32(v[u].x, h0, l0);
+          split_f32(v[u].y, h1, l1);
           reinterpret_cast<float2*>(hr)[q] = make_float2(h0, h1);
-          reinterpret_cast<float2*>(lr)[q] = make_float2(__double2float_rn(v[u].x - (double)h0),
-                                                         __double2float_rn(v[u].y - (double)h1));
+          reinterpret_cast<float2*>(lr)[q] = make_float2(l0, l1);
         }
       }
     }
     if ((d & 1) && lane == 0) {
-      const double x = xr[d - 1];
-      const float h = __double2float_rn(x);
+      float h, l;
+      split_f32(xr[d - 1], h, l);
       hr[d - 1] = h;
-      lr[d - 1] = __double2float_rn(x - (double)h);
+      lr[d - 1] = l;
     }
   }
 }
 
-spcg_status launch_to_f32(spcg_ctx* c) {
-  // one wave of resident CTAs: the grid-stride loop then has no tail wave
+static int to_f32_blocks_per_sm() {
   static int per_sm = 0;
   if (per_sm == 0) {
     int v = 0;
-    SPCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_to_f32, 256, 0));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_to_f32, 256, 0) != cudaSuccess) v = 1;
     per_sm = v > 0 ? v : 1;
   }
-  k_to_f32<<<per_sm * c->num_sms, 256, 0, c->stream>>>(c->X, c->ldx, c->N, c->d, c->Xf, c->Xl,
-                                                        c->ldxf);
+  return per_sm;
+}
+
+spcg_status launch_to_f32(spcg_ctx* c) {
+  // one wave of resident CTAs: the grid-stride loop then has no tail wave
+  k_to_f32<<<to_f32_blocks_per_sm() * c->num_sms, 256, 0, c->stream>>>(
+      c->X, c->ldx, c->N, c->d, c->Xf, c->Xl, c->ldxf);
   SPCG_CK(cudaGetLastError());
   c->n_launch += 1;
   return SPCG_OK;
 }
 
 }  // namespace spcg
+
+extern "C" spcg_status spcg_split_f32(const double* X, int64_t N, int32_t d, int64_t ldx,
+                                      float* Xh, float* Xl, int64_t ldxf, void* stream) {
+  if (N < 0 || d < 1 || ldx < d || ldxf < d) return SPCG_E_INVALID_ARG;
+  if (N == 0) return SPCG_OK;
+  if (!X || !Xh || !Xl || (ldx & 1) || (ldxf & 1) || ((uintptr_t)X & 15u) ||
+      ((uintptr_t)Xh & 7u) || ((uintptr_t)Xl & 7u))
+    return SPCG_E_INVALID_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SPCG_E_CUDA;
+  spcg::k_to_f32<<<spcg::to_f32_blocks_per_sm() * sms, 256, 0, (cudaStream_t)stream>>>(
+      X, ldx, N, d, Xh, Xl, ldxf);
+  if (cudaGetLastError() != cudaSuccess) return SPCG_E_CUDA;
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? SPCG_OK : SPCG_E_CUDA;
+}

@@ -146,6 +146,8 @@ _SIGS = {
     "spcg_gram_apply": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
     "spcg_gram_apply_typed": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                              _P, _P]),
+    "spcg_split_f32": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P, _P,
+                                      ctypes.c_int64, _P]),
     "spcg_resid_apply_typed": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64,
                                               ctypes.c_int64, _P, _P, _P]),
     "spcg_batch_create": (ctypes.c_int, [ctypes.POINTER(ProblemF32), ctypes.c_int32, _P,
@@ -434,6 +436,24 @@ class Solver:
         st = lib().spcg_gram_apply(self.ctx, _ptr(A) if m > 0 else None, m, lda, _ptr(p), _ptr(w))
         _check(st, "spcg_gram_apply")
         return w
+
+
+def spcg_split_f32(X, Xh=None, Xl=None, stream=None):
+    """(Xh, Xl) = the double-FP32 split of a row-major CUDA FP64 matrix X
+    (its rows 16-byte aligned), as FP32 tensors of X's shape."""
+    import torch
+    N, d = X.shape
+    ldx = X.stride(0) if N > 0 else d
+    if Xh is None:
+        ld = (d + 1) // 2 * 2
+        Xh = torch.zeros((N, ld), dtype=torch.float32, device=X.device)[:, :d]
+        Xl = torch.zeros((N, ld), dtype=torch.float32, device=X.device)[:, :d]
+    ldxf = Xh.stride(0) if N > 0 else d
+    st = lib().spcg_split_f32(_ptr(X) if N > 0 else None, N, d, ldx,
+                              _ptr(Xh) if N > 0 else None, _ptr(Xl) if N > 0 else None, ldxf,
+                              stream)
+    _check(st, "spcg_split_f32")
+    return Xh, Xl
 
 
 def spcg_candidate_schedule(N, d, idx):

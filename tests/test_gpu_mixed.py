@@ -220,3 +220,35 @@ def test_auto_rule_keeps_fp32_when_well_conditioned():
     assert info.cond_est * 2.0 ** -24 <= 1.0 / 32
     assert info.inner_prec == S.INNER_F32
     assert info.grad_prec == S.GRAD_DF
+
+
+def _split_cases():
+    rng = np.random.default_rng(11)
+    parts = [rng.standard_normal(4000) * 10.0 ** rng.uniform(-20, 20, 4000),
+             rng.standard_normal(1000) * 2.0 ** rng.integers(-80, -60, 1000),   # near 2^-74
+             rng.standard_normal(1000) * 2.0 ** rng.integers(120, 127, 1000),   # near 2^127
+             np.array([0.0, -0.0, 1.0, -1.0, 2.0 ** -74, 2.0 ** -75, 2.0 ** 126, 3e-320])]
+    # exact ties of the float rounding (the 29 dropped bits are 100...0), both parities
+    base = rng.standard_normal(1000)
+    bits = base.view(np.uint64) & ~np.uint64(0x1FFFFFFF) | np.uint64(0x10000000)
+    parts.append(bits.view(np.float64))
+    # values whose rounding carries into the exponent (fraction bits all ones)
+    ones = rng.standard_normal(500).view(np.uint64) | np.uint64(0xFFFFFFFFFFFFF)
+    parts.append(ones.view(np.float64))
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("d", [1, 7, 64, 257])
+def test_split_f32_is_round_to_nearest(d):
+    """Xh = fl32(x), Xl = fl32(x - Xh), bit for bit against numpy's rounding."""
+    v = _split_cases()
+    N = (len(v) + d - 1) // d
+    x = np.resize(v, N * d).reshape(N, d)
+    ld = (d + 1) // 2 * 2
+    Xd = torch.zeros((N, ld), dtype=torch.float64, device="cuda")
+    Xd[:, :d] = cuda(x)
+    Xh, Xl = S.spcg_split_f32(Xd[:, :d])
+    h_ref = x.astype(np.float32)
+    l_ref = (x - h_ref.astype(np.float64)).astype(np.float32)
+    assert np.array_equal(Xh.cpu().numpy().view(np.uint32), h_ref.view(np.uint32))
+    assert np.array_equal(Xl.cpu().numpy().view(np.uint32), l_ref.view(np.uint32))
