@@ -945,16 +945,31 @@ __device__ __forceinline__ void ts(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Consumer warps of the pair pass: wide rows (NI = 32) keep the direction
+// in shared memory instead of registers, which leaves room for 15 consumers
+// (the dependent TwoSum chains need the extra warps to hide their latency;
+// 15 consumers plus the producer make 512 threads, which leaves 128 registers
+// a thread).
 template <int NI>
-__global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
+struct DfCfg {
+  static constexpr int C = NI >= 32 ? 15 : kConsumers;
+  static constexpr int THREADS = 32 * (C + 1);
+  static constexpr bool PREG = NI <= 16;     // direction pair in registers
+  static constexpr bool XCACHE = NI <= 16;   // row kept in registers between the two products
+};
+constexpr int kDfMaxConsumers = 15;
+
+template <int NI>
+__global__ void __launch_bounds__(DfCfg<NI>::THREADS, 1)
     k_pass_df(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUtensorMap tml,
               const PassArgs a) {
-  constexpr int KC = PassCfg<NI>::C;
+  constexpr int KC = DfCfg<NI>::C;
+  constexpr bool PREG = DfCfg<NI>::PREG;
   // lanes own runs of V = 4 consecutive columns (one float4 of each half)
   constexpr int V = 4;
   constexpr int NG = (NI * 32 + 32 * V - 1) / (32 * V);
   constexpr int RS = NG * 32 * V;
-  constexpr bool XCACHE = NI <= 16;   // keep the row in registers between the two products
+  constexpr bool XCACHE = DfCfg<NI>::XCACHE;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base_addr = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((128u - (base_addr & 127u)) & 127u);
@@ -1029,14 +1044,16 @@ __global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
       const int c0 = g * 32 * V + lane * V;
       off[g] = (c0 < a.d) ? (c0 / a.boxc) * (int)a.slot_elems + (c0 % a.boxc) : -1;
     }
-    float ph[NG][V], pl[NG][V];
+    float ph[PREG ? NG : 1][V], pl[PREG ? NG : 1][V];
+    if constexpr (PREG) {
 #pragma unroll
-    for (int g = 0; g < NG; ++g)
+      for (int g = 0; g < NG; ++g)
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        ph[g][v] = vh_s[g * 32 * V + lane * V + v];
-        pl[g][v] = vl_s[g * 32 * V + lane * V + v];
-      }
+        for (int v = 0; v < V; ++v) {
+          ph[g][v] = vh_s[g * 32 * V + lane * V + v];
+          pl[g][v] = vl_s[g * 32 * V + lane * V + v];
+        }
+    }
     const int lo_off = a.nbox * (int)a.slot_elems;
     for (int k = 0; k < my_tiles; ++k) {
       const int s = k % a.stages;
@@ -1061,14 +1078,27 @@ __global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
           const float4 h4 = *reinterpret_cast<const float4*>(rh + off[g]);
           const float4 l4 = *reinterpret_cast<const float4*>(rl + off[g]);
           const float xa[V] = {h4.x, h4.y, h4.z, h4.w}, xb[V] = {l4.x, l4.y, l4.z, l4.w};
+          float qh[V], ql[V];
+          if constexpr (PREG) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              qh[v] = ph[PREG ? g : 0][v];
+              ql[v] = pl[PREG ? g : 0][v];
+            }
+          } else {
+            const float4 a4 = *reinterpret_cast<const float4*>(vh_s + g * 32 * V + lane * V);
+            const float4 b4 = *reinterpret_cast<const float4*>(vl_s + g * 32 * V + lane * V);
+            qh[0] = a4.x; qh[1] = a4.y; qh[2] = a4.z; qh[3] = a4.w;
+            ql[0] = b4.x; ql[1] = b4.y; ql[2] = b4.z; ql[3] = b4.w;
+          }
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            const float pr = __fmul_rn(xa[v], ph[g][v]);
-            const float pe = fmaf(xa[v], ph[g][v], -pr);
+            const float pr = __fmul_rn(xa[v], qh[v]);
+            const float pe = fmaf(xa[v], qh[v], -pr);
             float s2, se;
             ts(sh, pr, s2, se);
             sh = s2;
-            sl += pe + se + fmaf(xa[v], pl[g][v], xb[v] * ph[g][v]);
+            sl += pe + se + fmaf(xa[v], ql[v], xb[v] * qh[v]);
             if constexpr (XCACHE) {
               xh[g][v] = xa[v];
               xl[g][v] = xb[v];
@@ -1210,7 +1240,7 @@ spcg_status make_pass_geom_df(const float* Xh, const float* Xl, int64_t m, int d
   h.stage_bytes = stage;
   const size_t ni32 = (size_t)ni_for(d) * 32;
   const size_t cover = ni32 > 256 ? ni32 : 256;   // RS of k_pass_df is at most this
-  size_t red = (size_t)kConsumers * cover * 8;
+  size_t red = (size_t)kDfMaxConsumers * cover * 8;
   size_t tiles = stage * stages;
   if (tiles < red) tiles = red;
   h.region_bytes = tiles;
@@ -1229,7 +1259,7 @@ static spcg_status launch_df_ni(spcg_ctx* c, const PassGeom& g, const CUtensorMa
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1));
   if (e0) SPCG_CK(cudaEventRecord(e0, c->stream));
-  k_pass_df<NI><<<grid, PassCfg<NI>::THREADS, g.smem_bytes, c->stream>>>(g.tmap, tml, a);
+  k_pass_df<NI><<<grid, DfCfg<NI>::THREADS, g.smem_bytes, c->stream>>>(g.tmap, tml, a);
   SPCG_CK(cudaGetLastError());
   if (e1) SPCG_CK(cudaEventRecord(e1, c->stream));
   c->n_launch += 1;
