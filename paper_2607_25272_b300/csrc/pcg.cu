@@ -69,9 +69,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 constexpr int kConsumers = 12;                // consumer warps of k_pass (upper bound)
 // Consumer warps per CTA: fewer for the widest rows, whose accumulators need
 // the registers.
-template <int NI>
+// (Registers come in blocks of four warps: 13 warps get no more registers
+// than 16 would, 12 warps get as many as 12.)
+template <int NI, int ES = 8>   // ES: element size of the operand
 struct PassCfg {
-  static constexpr int C = NI >= 32 ? 8 : kConsumers;
+  static constexpr int C = NI < 32 ? kConsumers : (ES == 8 ? 8 : (ES == 4 ? 11 : kConsumers));
   static constexpr int THREADS = 32 * (C + 1);
 };
 constexpr int kMaxStages = 8;
@@ -199,9 +201,9 @@ template <> struct PassElem<__nv_bfloat16> {
 };
 
 template <typename T, int NI>
-__global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
+__global__ void __launch_bounds__(PassCfg<NI, sizeof(T)>::THREADS, 1)
     k_pass(const __grid_constant__ CUtensorMap tmap, const PassArgs a) {
-  constexpr int kConsumers = PassCfg<NI>::C;
+  constexpr int kConsumers = PassCfg<NI, sizeof(T)>::C;
   using E = PassElem<T>;
   // Each consumer lane owns runs of V consecutive columns (one 16-byte vector
   // of the row in shared memory), NG runs in all, RS columns covered.
@@ -292,8 +294,11 @@ __global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
     }
   } else {
     // ---- consumers: t = a_row . v (warp all-reduce), acc += t a_row ----
-    constexpr bool WIDE = NI >= 32 || sizeof(acc_t) == 8;   // p and the row from shared memory
-    constexpr int RW = (sizeof(acc_t) == 4 && !WIDE) ? 2 : 1;   // rows in flight per warp
+    // WIDE: p and the row come from shared memory (FP64 rows, and FP32 rows
+    // of more than 512 columns, whose compensated accumulators fill the
+    // registers); otherwise both stay in registers
+    constexpr bool WIDE = (NI >= 32 && E::compensated) || sizeof(acc_t) == 8;
+    constexpr int RW = (sizeof(acc_t) == 4 && !WIDE && NI < 32) ? 2 : 1;   // rows in flight
     constexpr int FLUSH = 8;                                     // tiles per compensated flush
     const int cw = warp - 1;
     int off[NG];
@@ -340,14 +345,26 @@ __global__ void __launch_bounds__(PassCfg<NI>::THREADS, 1)
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
           if (off[g] < 0) continue;
+          acc_t pq[V];
+          if constexpr (WIDE) {   // 16-byte loads of this lane's V entries of p
+            const int4* src = reinterpret_cast<const int4*>(vec_s + g * 32 * V + lane * V);
+            constexpr int NV = (int)(V * sizeof(acc_t) / 16);
+#pragma unroll
+            for (int u = 0; u < NV; ++u) {
+              const int4 raw = src[u];
+              memcpy(&pq[u * (16 / sizeof(acc_t))], &raw, 16);
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) pq[v] = pv[WIDE ? 0 : g][v];
+          }
 #pragma unroll
           for (int q = 0; q < RW; ++q) {
             acc_t x[V];
             E::load_vec(rowp[q] + off[g], x);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-              const acc_t pp = WIDE ? vec_s[g * 32 * V + lane * V + v] : pv[WIDE ? 0 : g][v];
-              t[q] = fma(x[v], pp, t[q]);
+              t[q] = fma(x[v], pq[v], t[q]);
               if constexpr (!WIDE) xr[q][g][v] = x[v];
             }
           }
@@ -664,7 +681,7 @@ static spcg_status launch_pass_ni(spcg_ctx* c, const PassGeom& g, const PassArgs
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1));
   if (e0) SPCG_CK(cudaEventRecord(e0, c->stream));
-  k_pass<T, NI><<<grid, PassCfg<NI>::THREADS, g.smem_bytes, c->stream>>>(g.tmap, a);
+  k_pass<T, NI><<<grid, PassCfg<NI, sizeof(T)>::THREADS, g.smem_bytes, c->stream>>>(g.tmap, a);
   SPCG_CK(cudaGetLastError());
   if (e1) SPCG_CK(cudaEventRecord(e1, c->stream));
   c->n_launch += 1;

@@ -53,7 +53,7 @@ def mixed_opts():
 
 
 @pytest.mark.parametrize("m,d", [(1, 1), (1000, 33), (4097, 256), (3001, 257), (100003, 50),
-                                 (20000, 500), (513, 1000)])
+                                 (20000, 500), (513, 1000), (20011, 1000)])
 def test_fp32_pass_parity(m, d):
     rng = np.random.default_rng(m + 3 * d)
     A32 = rng.standard_normal((m, d)).astype(np.float32)
@@ -72,7 +72,8 @@ def test_fp32_pass_parity(m, d):
     assert np.all(np.abs(w - ref) <= bound)
 
 
-@pytest.mark.parametrize("m,d", [(1, 1), (1000, 33), (4097, 256), (100003, 50), (20000, 500)])
+@pytest.mark.parametrize("m,d", [(1, 1), (1000, 33), (4097, 256), (100003, 50), (20000, 500),
+                                 (3001, 1000), (513, 777)])
 def test_bf16_pass_parity(m, d):
     rng = np.random.default_rng(m + 5 * d)
     At = torch.from_numpy(rng.standard_normal((m, d))).to(torch.bfloat16)
