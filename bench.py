@@ -46,9 +46,9 @@ WORKLOADS = {
 CPU_SAMPLE_ROWS = 1 << 17     # oracle row sample for the CPU baseline
 # DRAM bytes per algorithmic byte of k_pass (FP64) from one ncu capture of the
 # current kernel on a 262144 x 500 operand (profiles/k_pass_fp64_gram_262144x500.md):
-# read 1.048628 GB + wrote 3.604992 MB for 1.048576 GB of rows.  Set to None
+# read 1.048699 GB + wrote 3.254784 MB for 1.048576 GB of rows.  Set to None
 # whenever the kernel changes after the capture.
-K_PASS_TRAFFIC_RATIO = (1.048628e9 + 3.604992e6) / 1.048576e9
+K_PASS_TRAFFIC_RATIO = (1.048699e9 + 3.254784e6) / 1.048576e9
 
 
 def make_problem(w, N=None, seed_offset=0):
