@@ -63,6 +63,18 @@ def test_invalid_arguments_rejected_before_any_cuda_call():
     assert L.spcg_solve(None, 1, None, None, None) == S.SPCG_E_INVALID_ARG
     assert L.spcg_feistel(1, 31, 0, 1, 0, None, None) == S.SPCG_E_INVALID_ARG
     assert L.spcg_feistel(1, 4, 0, 17, 0, fake, None) == S.SPCG_E_INVALID_ARG
+    # residual and split entry points: null context, bad operand type, odd strides,
+    # misaligned pointers
+    assert L.spcg_resid_apply_typed(None, fake, 0, 10, 10, fake, fake, fake) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_gram_apply_typed(None, fake, 4, 10, 10, fake, fake) == S.SPCG_E_INVALID_ARG
+    f16 = ctypes.c_void_p(1 << 20)
+    assert L.spcg_split_f32(f16, 10, 5, 5, f16, f16, 6, None) == S.SPCG_E_INVALID_ARG    # odd ldx
+    assert L.spcg_split_f32(f16, 10, 5, 6, f16, f16, 5, None) == S.SPCG_E_INVALID_ARG    # odd ldxf
+    assert L.spcg_split_f32(ctypes.c_void_p((1 << 20) + 8), 10, 5, 6, f16, f16, 6,
+                            None) == S.SPCG_E_INVALID_ARG                              # X not 16-B
+    assert L.spcg_split_f32(f16, 10, 5, 4, f16, f16, 6, None) == S.SPCG_E_INVALID_ARG    # ldx < d
+    assert L.spcg_split_f32(f16, -1, 5, 6, f16, f16, 6, None) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_split_f32(None, 0, 5, 6, None, None, 6, None) == S.SPCG_OK             # N = 0
     L.spcg_destroy(None)   # no-op
 
 
