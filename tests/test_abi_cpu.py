@@ -112,3 +112,40 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+@pytest.mark.parametrize("N,d", [(1 << 20, 64), (70000, 129), (1 << 23, 256), (5000, 37)])
+def test_candidate_schedules_enumerate_the_learned_choice_set(N, d):
+    """The 25 candidates of the learned schedule: candidate 0 keeps only the
+    paper's first stage; candidate 1 + 6(g-1) + 3(s-1) + (a-2) adds stages
+    that grow by 2^s from the first up to N'/2^g, a iterations each
+    (g = 1..4, s = 1, 2, a = 2, 3, 4); candidate 2 is the paper's schedule."""
+    from oracle.spcg import default_schedule
+    paper = default_schedule(N, d)
+    n_pad = paper["n_pad"]
+    seen = set()
+    for idx in range(25):
+        c = S.spcg_candidate_schedule(N, d, idx)
+        m, a = list(c.m[: c.K]), list(c.a[: c.K])
+        if not paper["m"]:
+            assert c.K == 0
+            continue
+        m1 = paper["m"][0]
+        assert m[0] == m1 and a[0] == 3
+        if idx == 0:
+            assert c.K == 1
+        else:
+            g, rem = 1 + (idx - 1) // 6, (idx - 1) % 6
+            s, ai = 1 + rem // 3, 2 + rem % 3
+            want, mm = [m1], m1 << s
+            while mm <= n_pad >> g:
+                want.append(mm)
+                mm <<= s
+            assert m == want and a == [3] + [ai] * (len(want) - 1)
+        assert all(x <= n_pad // 2 for x in m)
+        seen.add(tuple(m + a))
+    if paper["m"]:
+        c2 = S.spcg_candidate_schedule(N, d, 2)
+        assert list(c2.m[: c2.K]) == paper["m"] and list(c2.a[: c2.K]) == paper["a"]
+    with pytest.raises(S.SpcgError):
+        S.spcg_candidate_schedule(N, d, 25)
