@@ -665,11 +665,6 @@ int tile_rows_for(int d, int chunk_bytes) {
   if (rows < 1) rows = 1;
   return rows;
 }
-int64_t next_pow2_h(int64_t n) {
-  int64_t p = 1;
-  while (p < n) p <<= 1;
-  return p;
-}
 }  // namespace
 
 using namespace spcg;
