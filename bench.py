@@ -363,7 +363,9 @@ def cpu_baseline(w, steps=1):
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
-    base = cpu_baseline(w, steps=1)                        # warm-up of the oracle arm
+    base = None
+    for _ in range(max(args.warmup, 1)):                   # warm-ups of the oracle arm
+        base = cpu_baseline(w, steps=1)
     vals = []
     for _ in range(args.steps):
         vals.append(cpu_baseline(w, steps=1)["value"])
