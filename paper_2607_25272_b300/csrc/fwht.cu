@@ -500,13 +500,13 @@ __global__ void __launch_bounds__(256) k_to_f32(const double* __restrict__ X, in
   }
 }
 
+// Resident CTAs per SM of k_to_f32, computed once (thread-safe static).
 static int to_f32_blocks_per_sm() {
-  static int per_sm = 0;
-  if (per_sm == 0) {
+  static const int per_sm = []() {
     int v = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_to_f32, 256, 0) != cudaSuccess) v = 1;
-    per_sm = v > 0 ? v : 1;
-  }
+    return v > 0 ? v : 1;
+  }();
   return per_sm;
 }
 
