@@ -372,8 +372,10 @@ __global__ void __launch_bounds__(PassCfg<NI, sizeof(T)>::THREADS, 1)
 #pragma unroll
         for (int q = 0; q < RW; ++q) {
           t[q] = warp_allsum(t[q]);
-          if (a.mode == PASS_RESID) t[q] = (acc_t)a.b[row0 + rr + q * kConsumers] - t[q];
+          // b is read only for a live row: the second row in flight may lie
+          // past the operand's last row (b has exactly m entries)
           if (!live[q]) t[q] = (acc_t)0;
+          else if (a.mode == PASS_RESID) t[q] = (acc_t)a.b[row0 + rr + q * kConsumers] - t[q];
         }
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
@@ -681,7 +683,8 @@ static spcg_status launch_pass_ni(spcg_ctx* c, const PassGeom& g, const PassArgs
   SPCG_CK(cudaFuncSetAttribute(k_pass<T, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)g.smem_bytes));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1));
+  const int op = g.dtype == DT_F64 ? OP_F64 : (g.dtype == DT_F32 ? OP_F32 : OP_BF16);
+  if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1, op));
   if (e0) SPCG_CK(cudaEventRecord(e0, c->stream));
   k_pass<T, NI><<<grid, PassCfg<NI, sizeof(T)>::THREADS, g.smem_bytes, c->stream>>>(g.tmap, a);
   SPCG_CK(cudaGetLastError());
@@ -689,6 +692,8 @@ static spcg_status launch_pass_ni(spcg_ctx* c, const PassGeom& g, const PassArgs
   c->n_launch += 1;
   c->n_pass += 1;
   c->pass_bytes += (uint64_t)g.m * g.d * g.esize;
+  c->n_pass_op[op] += 1;
+  c->pass_bytes_op[op] += (uint64_t)g.m * g.d * g.esize;
   return SPCG_OK;
 }
 
@@ -1276,7 +1281,7 @@ static spcg_status launch_df_ni(spcg_ctx* c, const PassGeom& g, const CUtensorMa
   SPCG_CK(cudaFuncSetAttribute(k_pass_df<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)g.smem_bytes));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1));
+  if (c->opts.profile) SPCG_TRY(prof_events(c, &e0, &e1, OP_PAIR));
   if (e0) SPCG_CK(cudaEventRecord(e0, c->stream));
   k_pass_df<NI><<<grid, DfCfg<NI>::THREADS, g.smem_bytes, c->stream>>>(g.tmap, tml, a);
   SPCG_CK(cudaGetLastError());
@@ -1284,6 +1289,8 @@ static spcg_status launch_df_ni(spcg_ctx* c, const PassGeom& g, const CUtensorMa
   c->n_launch += 1;
   c->n_pass += 1;
   c->pass_bytes += (uint64_t)g.m * g.d * 8;
+  c->n_pass_op[OP_PAIR] += 1;
+  c->pass_bytes_op[OP_PAIR] += (uint64_t)g.m * g.d * 8;
   return SPCG_OK;
 }
 
