@@ -11,6 +11,7 @@
 // object.  The address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, by the first call on that
 // device; that first call should therefore come before any stream capture.
+// A failed lookup is not remembered: the next call on that device tries again.
 //
 // All calls share the array and it keeps the last call's contents: the
 // status word is cleared on the caller's stream before each launch, and the
@@ -40,13 +41,37 @@ static_assert(sizeof(spcg::DevScalars) <= kScalarBytes, "scalar block outgrew it
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
+// Per-device result of the one-time lookup.  Only a successful lookup is
+// kept: an error (for example one left behind by an unrelated asynchronous
+// launch) is returned to that call, and the next call tries again.
 struct DeviceSlot {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
+  std::mutex mu;
   void* addr = nullptr;
   int sms = 0;
 };
 DeviceSlot g_slots[kMaxDevices];
+
+// The scratch array's device address and the SM count on device `dev`
+// (the current device).
+cudaError_t device_slot(int dev, void** addr, int* sms) {
+  DeviceSlot& slot = g_slots[dev];
+  std::lock_guard<std::mutex> lock(slot.mu);
+  if (!slot.addr) {
+    void* a = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return e;
+    }
+    slot.sms = n;
+    slot.addr = a;
+  }
+  *addr = slot.addr;
+  *sms = slot.sms;
+  return cudaSuccess;
+}
 
 }  // namespace
 
@@ -60,13 +85,9 @@ extern "C" spcg_status spcg_gram_apply_noalloc(const double* A, int64_t m, int32
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return from_cuda(cudaErrorInvalidDevice);
   if (dev < 0 || dev >= kMaxDevices) return SPCG_E_INVALID_ARG;
-  DeviceSlot& slot = g_slots[dev];
-  std::call_once(slot.once, [&]() {
-    slot.err = cudaGetSymbolAddress(&slot.addr, g_noalloc_scratch);
-    if (slot.err == cudaSuccess)
-      slot.err = cudaDeviceGetAttribute(&slot.sms, cudaDevAttrMultiProcessorCount, dev);
-  });
-  if (slot.err != cudaSuccess || !slot.addr) return SPCG_E_CUDA;
+  void* scratch = nullptr;
+  int sms = 0;
+  if (device_slot(dev, &scratch, &sms) != cudaSuccess || !scratch) return SPCG_E_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
   if (m == 0) {
     SPCG_CK(cudaMemsetAsync(w, 0, (size_t)d * sizeof(double), st));
@@ -75,14 +96,14 @@ extern "C" spcg_status spcg_gram_apply_noalloc(const double* A, int64_t m, int32
   }
   PassGeom g;
   SPCG_TRY(make_pass_geom(A, m, d, lda, &g));
-  int grid = slot.sms < kNoAllocMaxCtas ? slot.sms : kNoAllocMaxCtas;
+  int grid = sms < kNoAllocMaxCtas ? sms : kNoAllocMaxCtas;
   if (grid > g.ntiles) grid = g.ntiles;
   if (grid < 1) grid = 1;
   int ni = 1;
   while (ni * 32 < d) ni <<= 1;
   const int ldp = ni * 32;   // <= SPCG_MAX_D
-  DevScalars* scal = reinterpret_cast<DevScalars*>(slot.addr);
-  double* partials = reinterpret_cast<double*>(static_cast<unsigned char*>(slot.addr) + kScalarBytes);
+  DevScalars* scal = reinterpret_cast<DevScalars*>(scratch);
+  double* partials = reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) + kScalarBytes);
   SPCG_CK(cudaMemsetAsync(scal, 0, sizeof(DevScalars), st));
   SPCG_TRY(launch_gram_with_scratch(g, p, w, partials, ldp, grid, scal, st));
   int status = 0;

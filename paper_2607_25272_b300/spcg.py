@@ -50,6 +50,7 @@ GRAD_DF = 2
 SKETCH_SRHT = 0
 SKETCH_COUNT = 1
 DTYPE_CODE = {"float64": 0, "float32": 1, "bfloat16": 2}
+OP_NAMES = ("float64", "float32", "bfloat16", "pair")   # spcg_info.*_by_op order
 
 
 class SpcgError(RuntimeError):
@@ -85,6 +86,7 @@ class Opts(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("inner_prec", ctypes.c_int32),
         ("grad_prec", ctypes.c_int32),
+        ("max_workspace_bytes", ctypes.c_int64),
     ]
 
 
@@ -107,6 +109,9 @@ class Info(ctypes.Structure):
         ("cond_est", ctypes.c_double),
         ("inner_prec", ctypes.c_int32),
         ("grad_prec", ctypes.c_int32),
+        ("pass_ms_by_op", ctypes.c_double * 4),
+        ("bytes_by_op", ctypes.c_uint64 * 4),
+        ("launches_by_op", ctypes.c_int32 * 4),
     ]
 
 
@@ -178,6 +183,11 @@ _SIGS = {
     "spcg_mlp_to_bf16": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
     "spcg_gram_apply_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                                _P, _P, _P]),
+    "spcg_probe_fma_tflops": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_double), _P]),
+    "spcg_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                       ctypes.c_uint64, ctypes.POINTER(Schedule),
+                                       ctypes.POINTER(Opts), _P, _P, ctypes.POINTER(Info)]),
 }
 
 
@@ -499,29 +509,58 @@ def spcg_gram_apply_noalloc(A, p, w=None, stream=None):
     For callers that may not allocate device memory: the library uses its own
     fixed device scratch array (shared by all calls; calls that overlap on the
     GPU race).  The output w may be supplied so that nothing is allocated here
-    either."""
+    either.  A: row-major float64 CUDA matrix (stride(1) == 1); p, w: float64
+    CUDA vectors of d entries on A's device.  The call runs with A's device
+    current, since the C side works on the current device."""
     import torch
+    if A.dim() != 2 or A.dtype != torch.float64 or (A.shape[0] > 0 and A.stride(1) != 1):
+        raise ValueError("A must be a row-major 2-D float64 tensor")
     m, d = A.shape
+    if p.dtype != torch.float64 or p.numel() != d or p.device != A.device:
+        raise ValueError("p must be a float64 vector of d entries on A's device")
     if w is None:
-        w = torch.empty(d, dtype=torch.float64, device=p.device)
+        with torch.cuda.device(A.device):
+            w = torch.empty(d, dtype=torch.float64, device=A.device)
+    if w.dtype != torch.float64 or w.numel() != d or w.device != A.device:
+        raise ValueError("w must be a float64 vector of d entries on A's device")
     lda = A.stride(0) if m > 0 else d
-    st = lib().spcg_gram_apply_noalloc(_ptr(A) if m > 0 else None, m, d, lda, _ptr(p), _ptr(w),
-                                       _stream_ptr(stream))
+    with torch.cuda.device(A.device):
+        st = lib().spcg_gram_apply_noalloc(_ptr(A) if m > 0 else None, m, d, lda, _ptr(p),
+                                           _ptr(w), _stream_ptr(stream))
     _check(st, "spcg_gram_apply_noalloc")
     return w
 
 
-def spcg_solve_host(X_host, Y_host, seed, sched=None, opts=None):
-    """End-to-end call from pinned host buffers: H2D copy, solve, D2H of beta."""
+def spcg_probe_fma_tflops(dtype="float64", iters=1 << 16, stream=None):
+    """Measured FMA rate of the current GPU in TFLOP/s (2 flops per FMA) for
+    float64 or float32: the roofline denominator of an FMA-bound kernel."""
+    out = ctypes.c_double(0.0)
+    code = {"float64": 0, "float32": 1}[dtype]
+    _check(lib().spcg_probe_fma_tflops(code, int(iters), ctypes.byref(out), _stream_ptr(stream)),
+           "spcg_probe_fma_tflops")
+    return out.value
+
+
+def spcg_solve_host(X_host, Y_host, seed, sched=None, opts=None, stream=None):
+    """End to end from host memory through the C ABI (spcg_solve_host): the
+    library copies X and Y to the device, solves, and copies beta back.
+    X_host: row-major float64 CPU tensor (pinned memory copies fastest),
+    Y_host: float64 CPU vector.  Returns (beta as a CPU tensor, info, status)."""
     import torch
-    X = X_host.to("cuda", non_blocking=True)
-    Y = Y_host.to("cuda", non_blocking=True)
-    s = Solver(X, Y, opts)
-    try:
-        beta, info, st = s.solve(seed, sched)
-        return beta.cpu(), info, st
-    finally:
-        s.close()
+    if X_host.is_cuda or Y_host.is_cuda:
+        raise ValueError("X_host and Y_host must be CPU tensors")
+    if X_host.dtype != torch.float64 or Y_host.dtype != torch.float64 or X_host.stride(1) != 1:
+        raise ValueError("X_host must be a row-major float64 matrix and Y_host float64")
+    N, d = X_host.shape
+    beta = torch.empty(d, dtype=torch.float64)
+    info = Info()
+    st = lib().spcg_solve_host(ctypes.c_void_p(X_host.data_ptr()), ctypes.c_void_p(Y_host.data_ptr()),
+                               N, d, X_host.stride(0), seed,
+                               ctypes.byref(sched) if sched else None,
+                               ctypes.byref(opts) if opts is not None else None,
+                               _stream_ptr(stream), ctypes.c_void_p(beta.data_ptr()),
+                               ctypes.byref(info))
+    return beta, info, st
 
 
 class Batch:

@@ -44,9 +44,18 @@ def test_noalloc_pass_matches_context_pass_twice(m, d):
     w_ctx = solver.gram_apply(Av, pd).cpu().numpy()
     solver.close()
     bound = 2 * gamma(m + d) * (np.abs(A).T @ (np.abs(A) @ np.abs(p)))
-    for _ in range(2):
+    for call in range(2):
         w = torch.full((d,), np.nan, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
         S.spcg_gram_apply_noalloc(Av, pd, w)
+        torch.cuda.synchronize()
+        if call == 1:
+            # the property the entry point exists for: the second call (the
+            # first may load the kernels' module) takes no device memory
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == alloc0
         w = w.cpu().numpy()
         assert np.all(np.abs(w - w_ctx) <= bound)
         assert np.all(np.abs(w - A.T @ (A @ p)) <= bound)
@@ -61,3 +70,18 @@ def test_noalloc_rejects_too_many_columns():
     with pytest.raises(S.SpcgError) as e:
         S.spcg_gram_apply_noalloc(A, p)
     assert e.value.status == S.SPCG_E_INVALID_ARG
+
+
+def test_noalloc_binding_rejects_wrong_dtype_and_layout():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    A = torch.zeros((8, 4), dtype=torch.float32, device="cuda")
+    p = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        S.spcg_gram_apply_noalloc(A, p)
+    At = torch.zeros((4, 8), dtype=torch.float64, device="cuda").T   # column-major view
+    with pytest.raises(ValueError):
+        S.spcg_gram_apply_noalloc(At, p)
+    with pytest.raises(ValueError):
+        S.spcg_gram_apply_noalloc(torch.zeros((8, 4), dtype=torch.float64, device="cuda"),
+                                  torch.zeros(5, dtype=torch.float64, device="cuda"))
