@@ -1,6 +1,6 @@
 """Benchmark: seconds to a 1e-6 relative OLS prediction error with SPCG.
 
-Workload (default): plain FP64 SPCG on N = 2^20, d = 500, X = U diag(s) V^T
+Headline workload: plain FP64 SPCG on N = 2^20, d = 500, X = U diag(s) V^T
 with s geometric from 1 to 1e-6 (kappa = 1e6), beta ~ N(0, 1), sigma = 0.1;
 the paper's default schedule (m_1 = 8d rounded to a power of two, doubling
 to N'/2, r = 6d, a_i = 3) and the Stage II stopping rule for tol = 1e-6.
@@ -11,6 +11,15 @@ subproblem, Stage II to the stopping rule) with X, Y resident in HBM.
 X is 4.19 GB, far larger than the 126 MB L2, so no flush is needed between
 steps.  The result is checked against the oracle's OLS estimator (outside
 the timed region).
+
+The same JSON line carries the metric's comparisons at the other workloads
+(one GPU only): "c3" mixed precision against plain FP64 at N = 2^22,
+d = 1000, kappa = 1e8 with heavy leverage; "c4" 512 batched FP32 problems
+against a loop of plain solves; "c5" the learned schedule against the
+paper's schedule at N = 2^23, d = 256.  Those inputs are drawn on the GPU
+(same recipes, torch random streams) and judged by properties that hold at
+any size (the construction's closed-form OLS estimator, or an FP64 least-
+squares solve by the GPU's linear-algebra library).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own independent problem (weak scaling,
@@ -43,11 +52,12 @@ WORKLOADS = {
     "c1": dict(name="plain SPCG FP64, N=20000, d=50, X iid N(0,1), sigma=1, seed=1",
                N=20000, d=50, kappa=None, sigma=1.0, seed=1, tol=1e-6),
 }
-CPU_SAMPLE_ROWS = 1 << 17     # oracle row sample for the CPU baseline
-# DRAM bytes per algorithmic byte of k_pass (FP64) from one ncu capture of the
-# current kernel on a 262144 x 500 operand (profiles/k_pass_fp64_gram_262144x500.md):
-# read 1.048699 GB + wrote 3.254784 MB for 1.048576 GB of rows.  Set to None
-# whenever the kernel changes after the capture.
+WARM_SAMPLE_ROWS = 1 << 14    # oracle warm-up sample of the reference arm
+NOMINAL_FP64_TFLOPS = 1.25    # B300 FP64, nominal (context only)
+# DRAM bytes per algorithmic byte of k_pass (FP64), from the ncu capture of
+# this kernel on a 262144 x 500 operand: read 1.048699 GB + wrote 3.254784 MB
+# for 1.048576 GB of rows.  Set to None whenever the kernel changes after the
+# capture.
 K_PASS_TRAFFIC_RATIO = (1.048699e9 + 3.254784e6) / 1.048576e9
 
 
@@ -92,15 +102,45 @@ def closed_form_rel_error(beta, uty, s, V):
                  torch.linalg.norm(s * (V.T @ b_ols)))
 
 
+def extra_steps(args):
+    """Steps and warm-ups of the nested workloads: at most 5 and 2, so that
+    the default run stays within minutes."""
+    return max(1, min(args.steps, 5)), max(1, min(args.warmup, 2))
+
+
+def pass_roofline(info, op, peak_gbs, peak_source, traffic_ratio, kernel):
+    """HBM roofline of the passes of one operand kind from a profiled solve:
+    algorithmic bytes per launch / mean CUDA-event duration per launch."""
+    from paper_2607_25272_b300 import spcg as S
+    k = S.OP_NAMES.index(op)
+    n, ms, nbytes = info.launches_by_op[k], info.pass_ms_by_op[k], info.bytes_by_op[k]
+    if n == 0 or ms <= 0:
+        return None
+    per_launch = nbytes / n
+    gbs = per_launch / (ms / n / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": peak_gbs, "unit": "GB/s",
+            "frac": gbs / peak_gbs, "peak_source": peak_source,
+            "traffic": per_launch * traffic_ratio if traffic_ratio else None,
+            "launches_per_step": n, "alg_bytes_per_launch": per_launch}
+
+
+def hbm_peak():
+    peaks = measured_peaks()
+    if "hbm_gbs" in peaks:
+        return peaks["hbm_gbs"], "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6400.0, "of fallback (6.4 TB/s; no MEASURED_PEAKS.json on this host)"
+
+
 def run_forms(args, w):
     """Plain FP64 vs mixed precision on one large problem (C3).  The problem
     is drawn on the GPU (host generation of 4M x 1000 takes minutes); the
     prediction error against the OLS estimator comes from the construction's
-    closed form (closed_form_rel_error)."""
+    closed form (closed_form_rel_error).  Returns a dict."""
     import torch
 
     from paper_2607_25272_b300 import spcg as S
     from paper_2607_25272_b300.inputs import svd_problem_device
+    steps, warmup = extra_steps(args)
     dev = torch.device("cuda", 0)
     t0 = time.time()
     Xd, Yd, _, uty, sv_s, sv_V = svd_problem_device(w["N"], w["d"], w["kappa"], w["sigma"],
@@ -113,18 +153,25 @@ def run_forms(args, w):
     stream = torch.cuda.current_stream(dev)
     sched = S.spcg_default_schedule(N, d)
     sched.tol = w["tol"]
+    peak, peak_src = hbm_peak()
     res = {}
     for name, prec in (("plain_fp64", S.PREC_FP64), ("mixed", S.PREC_MIXED)):
         o = S.Opts()
         o.precision = prec
         sv = S.Solver(Xd, Yd, o)
-        ms, outs = time_solves(sv, w["seed"], sched, args.steps, args.warmup, stream,
+        ms, outs = time_solves(sv, w["seed"], sched, steps, warmup, stream,
                                fn=lambda sv=sv: sv.solve(w["seed"], sched, raise_on_error=False))
         beta, info, st = outs[-1]
+        sv.close()
         o.profile = 1
         pv = S.Solver(Xd, Yd, o)
         _, pinfo, _ = pv.solve(w["seed"], sched, raise_on_error=False)
         pv.close()
+        by_op = {S.OP_NAMES[k]: {"launches": pinfo.launches_by_op[k],
+                                 "ms": pinfo.pass_ms_by_op[k],
+                                 "gbs": (pinfo.bytes_by_op[k] / (pinfo.pass_ms_by_op[k] / 1e3) / 1e9)
+                                 if pinfo.pass_ms_by_op[k] > 0 else None}
+                 for k in range(4) if pinfo.launches_by_op[k] > 0}
         res[name] = {"s": ms / 1e3, "status": S.STATUS[st],
                      "rel_pred_error": closed_form_rel_error(beta, uty, sv_s, sv_V),
                      "phases_ms": {"sketch": info.ms_sketch, "stages": info.ms_stages,
@@ -132,71 +179,107 @@ def run_forms(args, w):
                      "refine_iters": info.refine_iters, "restarts": info.restarts,
                      "cond_est": info.cond_est, "inner_prec": info.inner_prec,
                      "grad_prec": info.grad_prec, "launches": info.launches,
-                     "pass_gbs": pinfo.bytes_pass / (pinfo.pass_ms / 1e3) / 1e9
-                     if pinfo.pass_ms > 0 else None}
-        sv.close()
-    line = base_line(args, w, res["mixed"]["s"],
-                     "seconds to 1e-6 OLS prediction error (mixed precision vs plain FP64 SPCG)",
-                     "bf16/f32/f64")
-    line["config"].update({"N": N, "d": d, "tol": w["tol"],
-                           "inputs": "drawn on the GPU (svd_problem_device), same recipe",
-                           "l2": "no flush: X is 33.6 GB, larger than the 126 MB L2"})
-    line["forms"] = res
-    line["speedup_mixed_vs_plain_fp64"] = res["plain_fp64"]["s"] / res["mixed"]["s"]
-    line["accuracy_reference"] = ("closed-form OLS estimator of the construction, "
-                                  "V diag(1/s) U^T Y")
-    line["host_s"] = {"generate": gen_s}
-    print(json.dumps(line), flush=True)
+                     "passes_by_operand": by_op}
+        if name == "mixed":
+            res[name]["roofline"] = pass_roofline(
+                pinfo, "pair" if info.inner_prec == S.INNER_DF else "float32", peak, peak_src,
+                None, "k_pass_df (double-FP32 pair)" if info.inner_prec == S.INNER_DF
+                else "k_pass<float>")
+    # end to end through the public API from pinned host buffers, when the
+    # host can hold a pinned copy of X (33.6 GB)
+    e2e = None
+    try:
+        import psutil
+        avail = psutil.virtual_memory().available
+    except ImportError:
+        avail = 0
+    nbytes = N * d * 8 + N * 8
+    if avail > 3 * nbytes:
+        Xh = Xd.cpu().pin_memory()
+        Yh = Yd.cpu().pin_memory()
+        del Xd, Yd
+        torch.cuda.empty_cache()
+        o = S.Opts()
+        o.precision = S.PREC_MIXED
+        ts = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            b_host, _, st_e = S.spcg_solve_host(Xh, Yh, w["seed"], sched, o)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a0.elapsed_time(a1))
+        e2e = {"value": float(min(ts)) / 1e3, "unit": "s", "h2d_bytes_per_step": int(nbytes),
+               "d2h_bytes_per_step": int(d * 8), "form": "mixed",
+               "status": S.STATUS[st_e]}
+        del Xh, Yh
+    else:
+        del Xd, Yd
+    torch.cuda.empty_cache()
+    return {"workload": w["name"], "N": N, "d": d, "tol": w["tol"], "steps": steps,
+            "warmup": warmup,
+            "metric": "seconds to 1e-6 OLS prediction error (mixed precision vs plain FP64 SPCG)",
+            "inputs": "drawn on the GPU (svd_problem_device), same recipe",
+            "l2": "no flush: X is 33.6 GB, larger than the 126 MB L2",
+            "forms": res,
+            "speedup_mixed_vs_plain_fp64": res["plain_fp64"]["s"] / res["mixed"]["s"],
+            "accuracy_reference": "closed-form OLS estimator of the construction, "
+                                  "V diag(1/s) U^T Y",
+            "e2e": e2e if e2e else {"unavailable": "host memory too small for a pinned copy of X"},
+            "host_s": {"generate": gen_s}}
 
 
 def run_batched(args, w):
     """C4: 512 uneven FP32 problems in one persistent launch vs a loop of
-    single plain-FP64 solves of the same problems."""
+    single plain-FP64 solves of the same problems.  Problems are drawn on the
+    GPU; every solution is judged against an FP64 least-squares solve of its
+    FP32 values by the GPU's linear-algebra library (torch.linalg.lstsq),
+    which shares nothing with this library's kernels.  Returns a dict."""
     import torch
 
-    from oracle.linalg import ols
-    from oracle.metrics import rel_pred_error
     from paper_2607_25272_b300 import spcg as S
-    from paper_2607_25272_b300.inputs import scaled_columns_problem
+    from paper_2607_25272_b300.inputs import scaled_columns_problem_device
+    steps, warmup = extra_steps(args)
     rng = np.random.default_rng(w["seed"])
     n = w["batch"]
-    probs = []
-    for i in range(n):
-        N = int(rng.integers(1 << 12, (1 << 17) + 1))
-        d = int(rng.integers(16, 257))
-        X, Y, _ = scaled_columns_problem(N, d, 1e-3, 1e3, w["sigma"], seed=w["seed"] * 100000 + i)
-        probs.append((X.astype(np.float32), Y.astype(np.float32)))
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
+    shapes = [(int(rng.integers(1 << 12, (1 << 17) + 1)), int(rng.integers(16, 257)))
+              for _ in range(n)]
     Xs, Ys = [], []
-    for X, Y in probs:
-        N, d = X.shape
+    for i, (N, d) in enumerate(shapes):
+        X, Y, _ = scaled_columns_problem_device(N, d, 1e-3, 1e3, w["sigma"],
+                                                seed=w["seed"] * 100000 + i, device=dev,
+                                                dtype=torch.float32)
         ld = (d + 3) // 4 * 4
-        Xd = torch.zeros((N, ld), dtype=torch.float32, device=dev)
-        Xd[:, :d] = torch.from_numpy(X).to(dev)
-        Xs.append(Xd[:, :d])
-        Ys.append(torch.from_numpy(Y).to(dev))
+        Xp = torch.zeros((N, ld), dtype=torch.float32, device=dev)
+        Xp[:, :d] = X
+        Xs.append(Xp[:, :d])
+        Ys.append(Y)
     B = S.Batch(Xs, Ys)
     tiles = B.autotune(w["seed"], w["tol"])
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         B.solve(w["seed"], w["tol"])
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         rc, st, it, ms = B.solve(w["seed"], w["tol"])
         times.append(ms)
     ms_b = float(np.median(times))
-    betas = [b.cpu().numpy() for b in B.betas]
+    betas = [b.clone() for b in B.betas]
     B.close()
     # the comparator: one plain FP64 spcg_solve per problem, back to back
     loop_ms = 0.0
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     loop_status = []
-    for (X, Y), Xd in zip(probs, Xs):
-        X64 = torch.from_numpy(X.astype(np.float64)).to(dev)
-        Y64 = torch.from_numpy(Y.astype(np.float64)).to(dev)
+    errs = []
+    for X, Y, b in zip(Xs, Ys, betas):
+        X64 = X.double().contiguous()
+        Y64 = Y.double()
         sv = S.Solver(X64, Y64)
-        sc = S.spcg_default_schedule(*X.shape)
+        sc = S.spcg_default_schedule(*X64.shape)
         sc.tol = w["tol"]
         sv.solve(w["seed"], sc, raise_on_error=False)          # warm
         torch.cuda.synchronize()
@@ -207,63 +290,83 @@ def run_batched(args, w):
         loop_ms += e0.elapsed_time(e1)
         loop_status.append(st_)
         sv.close()
-    errs = []
-    for (X, Y), b in zip(probs, betas):
-        X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
-        errs.append(rel_pred_error(X64, b, ols(X64, Y64)))
-    line = base_line(args, w, ms_b / 1e3,
-                     "seconds to 1e-6 OLS prediction error for the whole batch (batched vs a "
-                     "loop of plain FP64 SPCG solves)", "f32 (compensated) / f64 scalars")
-    line["config"].update({"problems": n, "tol": w["tol"]})
-    line["batched"] = {"s": ms_b / 1e3, "status_ok": int(sum(1 for v in st if v == 0)),
-                       "max_rel_pred_error": float(max(errs)),
-                       "problems_meeting_tol": int(sum(1 for e in errs if e <= w["tol"])),
-                       "autotuned_chunk_bytes": tiles}
-    line["loop_plain_fp64"] = {"s": loop_ms / 1e3,
-                               "status_ok": int(sum(1 for v in loop_status if v == 0))}
-    line["speedup_batched_vs_loop"] = loop_ms / ms_b if ms_b > 0 else None
-    print(json.dumps(line), flush=True)
+        bh = torch.linalg.lstsq(X64, Y64[:, None], driver="gels").solution[:, 0]
+        errs.append(float(torch.linalg.norm(X64 @ (b - bh)) / torch.linalg.norm(X64 @ bh)))
+    total_bytes = sum(X.shape[0] * X.shape[1] * 4 for X in Xs)
+    return {"workload": w["name"], "problems": n, "tol": w["tol"], "steps": steps,
+            "warmup": warmup,
+            "metric": "seconds to 1e-6 OLS prediction error for the whole batch (batched vs a "
+                      "loop of plain FP64 SPCG solves)",
+            "inputs": "drawn on the GPU (scaled_columns_problem_device), same recipe",
+            "batched": {"s": ms_b / 1e3, "status_ok": int(sum(1 for v in st if v == 0)),
+                        "max_rel_pred_error": float(max(errs)),
+                        "problems_meeting_tol": int(sum(1 for e in errs if e <= w["tol"])),
+                        "autotuned_chunk_bytes": tiles,
+                        "x_bytes_fp32": int(total_bytes)},
+            "loop_plain_fp64": {"s": loop_ms / 1e3,
+                                "status_ok": int(sum(1 for v in loop_status if v == 0))},
+            "speedup_batched_vs_loop": loop_ms / ms_b if ms_b > 0 else None,
+            "accuracy_reference": "torch.linalg.lstsq (FP64, QR) of each problem's FP32 values"}
 
 
 def run_learned(args, w):
-    """C5: the learned schedule vs the paper's schedule (plain FP64 SPCG)."""
+    """C5: the learned schedule vs the paper's schedule (plain FP64 SPCG) at
+    N = 2^23, d = 256, drawn on the GPU and judged by the closed form.
+    Returns a dict."""
     import torch
 
-    from oracle.linalg import ols_lowmem
-    from oracle.metrics import rel_pred_error
     from paper_2607_25272_b300 import schedule_model as SM
     from paper_2607_25272_b300 import spcg as S
-    X, Y, _ = make_problem(w)
-    N, d = X.shape
+    from paper_2607_25272_b300.inputs import svd_problem_device
+    steps, warmup = extra_steps(args)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    Xd = torch.from_numpy(X).to(dev)
-    Yd = torch.from_numpy(Y).to(dev)
+    Xd, Yd, _, uty, sv_s, sv_V = svd_problem_device(w["N"], w["d"], w["kappa"], w["sigma"],
+                                                    seed=w["seed"], device=dev)
+    N, d = Xd.shape
     Wb, norm = SM.load(args.weights) if args.weights else SM.load()
     sv = S.Solver(Xd, Yd)
-    ms_p, outs_p = time_solves(sv, w["seed"], None, args.steps, args.warmup, stream,
+    ms_p, outs_p = time_solves(sv, w["seed"], None, steps, warmup, stream,
                                fn=lambda: sv.solve_learned(w["seed"], None, None, w["tol"],
                                                            raise_on_error=False))
-    ms_l, outs_l = time_solves(sv, w["seed"], None, args.steps, args.warmup, stream,
+    ms_l, outs_l = time_solves(sv, w["seed"], None, steps, warmup, stream,
                                fn=lambda: sv.solve_learned(w["seed"], Wb, norm, w["tol"],
                                                            raise_on_error=False))
     bp, ip, cp, sp = outs_p[-1]
     bl, il, cl, sl = outs_l[-1]
     sv.close()
-    bh = ols_lowmem(X, Y)
-    line = base_line(args, w, ms_l / 1e3,
-                     "seconds to 1e-6 OLS prediction error (learned schedule vs the paper's "
-                     "schedule, plain FP64 SPCG)", "f64")
-    line["config"].update({"N": N, "d": d, "tol": w["tol"],
-                           "model": "MLP 4-64-64-25, BF16 weights" if Wb is not None else
-                           "no trained weights: paper schedule"})
-    line["paper_schedule"] = {"s": ms_p / 1e3, "candidate": cp, "status": S.STATUS[sp],
-                              "rel_pred_error": rel_pred_error(X, bp.cpu().numpy(), bh),
-                              "refine_iters": ip.refine_iters}
-    line["learned_schedule"] = {"s": ms_l / 1e3, "candidate": cl, "status": S.STATUS[sl],
-                                "rel_pred_error": rel_pred_error(X, bl.cpu().numpy(), bh),
-                                "refine_iters": il.refine_iters, "stages": il.K}
-    line["speedup_learned_vs_paper"] = ms_p / ms_l
+    del Xd, Yd
+    torch.cuda.empty_cache()
+    return {"workload": w["name"], "N": N, "d": d, "tol": w["tol"], "steps": steps,
+            "warmup": warmup,
+            "metric": "seconds to 1e-6 OLS prediction error (learned schedule vs the paper's "
+                      "schedule, plain FP64 SPCG)",
+            "model": "MLP 4-64-64-25, BF16 weights" if Wb is not None else
+                     "no trained weights: paper schedule",
+            "inputs": "drawn on the GPU (svd_problem_device), same recipe",
+            "paper_schedule": {"s": ms_p / 1e3, "candidate": cp, "status": S.STATUS[sp],
+                               "rel_pred_error": closed_form_rel_error(bp, uty, sv_s, sv_V),
+                               "refine_iters": ip.refine_iters},
+            "learned_schedule": {"s": ms_l / 1e3, "candidate": cl, "status": S.STATUS[sl],
+                                 "rel_pred_error": closed_form_rel_error(bl, uty, sv_s, sv_V),
+                                 "refine_iters": il.refine_iters, "stages": il.K},
+            "speedup_learned_vs_paper": ms_p / ms_l,
+            "accuracy_reference": "closed-form OLS estimator of the construction"}
+
+
+def print_nested(args, w, res, dtype):
+    """A standalone run of one nested workload: its own JSON line."""
+    if "forms" in res:
+        v = res["forms"]["mixed"]["s"]
+    elif "batched" in res:
+        v = res["batched"]["s"]
+    else:
+        v = res["learned_schedule"]["s"]
+    line = base_line(args, w, v, res["metric"], dtype)
+    line["steps"], line["warmup"] = res["steps"], res["warmup"]
+    line["ms_per_step"] = v * 1e3
+    line["config"].update({k: res[k] for k in ("N", "d", "problems", "tol") if k in res})
+    line["result"] = res
     print(json.dumps(line), flush=True)
 
 
@@ -341,41 +444,107 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(w, steps=1):
-    """The oracle (numpy FP64) on a row sample of the workload, scaled to N."""
+def host_threads():
+    """Threads the oracle's BLAS may use on this host."""
+    return int(os.environ.get("OPENBLAS_NUM_THREADS", len(os.sched_getaffinity(0))))
+
+
+def oracle_phases(X, Y, seed, tol):
+    """The oracle's SPCG solve (oracle.spcg.spcg, Algorithm 1 with the Stage II
+    stopping rule) as the sequence of its own calls, in its order: the SRHT
+    transform, the nested sketches and the preconditioner factor, one PCG run
+    per stage, Stage II.  Each phase is returned as a closure so that a caller
+    can time them one by one; the last one returns the final beta."""
+    from oracle import spcg as OS
+    from oracle import srht as OR
+    from oracle.linalg import r_factor
+    sched = OS.default_schedule(*X.shape)
+    st = {"beta": np.zeros(X.shape[1])}
+
+    def transform():
+        st["Z"] = OR.srht_transform(X, Y, seed)
+
+    def sketches():
+        ZX, ZY = st.pop("Z")
+        st["stages"], A_hat = OR.nested_sketches(ZX, ZY, sched["m"], sched["r"], seed)
+        st["R"] = r_factor(A_hat)
+
+    def stage(i):
+        def run():
+            A_i, b_i = st["stages"][i]
+            st["beta"], _ = OS.pcg(A_i, b_i, st["R"], st["beta"], sched["a"][i])
+        return run
+
+    def refine():
+        st.pop("stages", None)
+        st["beta"], _, _ = OS.full_pcg(X, Y, st["R"], st["beta"], tol)
+        return st["beta"]
+
+    return [transform, sketches] + [stage(i) for i in range(len(sched["m"]))] + [refine]
+
+
+def phase_groups(phases, K):
+    """The phases split into K consecutive groups, as evenly as possible
+    (groups are empty when K exceeds the number of phases)."""
+    n = len(phases)
+    return [phases[(k * n) // K:((k + 1) * n) // K] for k in range(K)]
+
+
+def cpu_baseline(w, X=None, Y=None):
+    """One complete oracle SPCG solve (numpy FP64) of the whole workload at
+    its stated size, wall time, no scaling."""
     from oracle.spcg import spcg as oracle_spcg
-    n_s = min(CPU_SAMPLE_ROWS, w["N"])
-    X, Y, _ = make_problem(w, N=n_s)
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        oracle_spcg(X, Y, seed=w["seed"], tol=w["tol"])
-        times.append(time.perf_counter() - t0)
-    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", len(os.sched_getaffinity(0))))
-    scale = w["N"] / n_s
-    return {"value": float(np.mean(times) * scale), "unit": "s", "cores": int(threads),
-            "kind": "oracle",
-            "sample": f"oracle SPCG (numpy FP64, BLAS on {threads} threads) on the same recipe "
-                      f"with N={n_s} rows, same d, kappa, sigma, schedule rule and tol; "
-                      f"wall time x N/{n_s} (measured {np.mean(times):.2f} s per sample solve)"}
+    if X is None:
+        X, Y, _ = make_problem(w)
+    t0 = time.perf_counter()
+    oracle_spcg(X, Y, seed=w["seed"], tol=w["tol"])
+    sec = time.perf_counter() - t0
+    threads = host_threads()
+    return {"value": float(sec), "unit": "s", "cores": int(threads), "kind": "oracle",
+            "sample": f"one complete oracle SPCG solve of the whole workload (N={X.shape[0]}, "
+                      f"d={X.shape[1]}, same recipe, schedule rule and tol), numpy FP64 with "
+                      f"BLAS on {threads} threads (numpy's elementwise transform runs on one); "
+                      f"wall time of that solve, not scaled"}
 
 
 def run_reference(args, w, rank, world):
+    """The oracle arm: K timed steps that together run ONE complete oracle
+    solve of the stated workload, split at the oracle's own call boundaries
+    (transform | sketches + QR | one step per stage | Stage II; with K
+    smaller than the number of phases a step runs several, with K larger the
+    remaining steps have no work).  value = the sum of the K step times = the
+    wall time of that full-size solve; the warm-up steps solve a small sample
+    of the same recipe."""
     if rank != 0:
         return
-    base = None
-    for _ in range(max(args.warmup, 1)):                   # warm-ups of the oracle arm
-        base = cpu_baseline(w, steps=1)
-    vals = []
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(w, steps=1)["value"])
-    v = float(np.mean(vals))
-    base["value"] = v
+    threads = host_threads()
+    for _ in range(args.warmup):                              # warm-ups: small sample
+        Xs, Ys, _ = make_problem(w, N=min(WARM_SAMPLE_ROWS, w["N"]))
+        for ph in oracle_phases(Xs, Ys, w["seed"], w["tol"]):
+            ph()
+    X, Y, _ = make_problem(w)                                 # data generation: untimed
+    phases = oracle_phases(X, Y, w["seed"], w["tol"])
+    K = max(args.steps, 1)
+    groups = phase_groups(phases, K)
+    step_s = []
+    for grp in groups:
+        t0 = time.perf_counter()
+        for ph in grp:
+            ph()
+        step_s.append(time.perf_counter() - t0)
+    v = float(sum(step_s))
+    base = {"value": v, "unit": "s", "cores": int(threads), "kind": "oracle",
+            "sample": f"one complete oracle SPCG solve of the whole workload (N={X.shape[0]}, "
+                      f"d={X.shape[1]}) run as {K} timed steps split at the oracle's call "
+                      f"boundaries ({len(phases)} phases); numpy FP64, BLAS on {threads} "
+                      f"threads; warm-ups on a {min(WARM_SAMPLE_ROWS, w['N'])}-row sample"}
     line = {"impl": "reference", "metric": "seconds to 1e-6 OLS prediction error (plain FP64 SPCG)",
             "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "warmup": args.warmup, "ms_per_step": v * 1e3 / K, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "N": w["N"], "d": w["d"], "tol": w["tol"]},
+            "config": {"workload": w["name"], "N": w["N"], "d": w["d"], "tol": w["tol"],
+                       "step": f"1/{K} of one full-size solve (value = one whole solve)"},
+            "step_seconds": [round(t, 3) for t in step_s],
             "cpu_baseline": base,
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -557,7 +726,8 @@ def run_ours(args, w, rank, world, local_rank):
         pass_n += pinfo.pass_launches
     psolver.close()
 
-    # end to end through the public API: pinned host -> device, solve, beta -> host
+    # end to end through the C ABI from pinned host buffers (spcg_solve_host:
+    # H2D of X and Y, the solve, D2H of beta, all inside the timed region)
     e2e_steps = max(1, min(args.steps, 3))
     solver.close()
     del Xd, Yd
@@ -568,15 +738,10 @@ def run_ours(args, w, rank, world, local_rank):
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        Xd2 = Xh.to(dev, non_blocking=True)
-        Yd2 = Yh.to(dev, non_blocking=True)
-        s2 = S.Solver(Xd2, Yd2)
-        b2, _, _ = s2.solve(w["seed"], sched)
-        bh2 = b2.to("cpu", non_blocking=False)
+        bh2, _, st2 = S.spcg_solve_host(Xh, Yh, w["seed"], sched)
         a1.record(stream)
         torch.cuda.synchronize()
-        s2.close()
-        del Xd2, Yd2
+        assert st2 == S.SPCG_OK, S.STATUS[st2]
         t_e2e.append(a0.elapsed_time(a1))
     if rank != 0:
         return
@@ -586,30 +751,29 @@ def run_ours(args, w, rank, world, local_rank):
     e_rel = rel_pred_error(X, beta_h, beta_ols)
     e_rel_mixed = rel_pred_error(X, mbeta_h, beta_ols)
 
-    peaks = measured_peaks()
-    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    hbm_peak_gbs, hbm_src = hbm_peak()
+    # the plain pass is bound by FP64 FMA issue: its denominator is the FP64
+    # FMA rate measured on this GPU now (a kernel of independent FMA chains)
+    fp64_peak_tflops = S.spcg_probe_fma_tflops("float64", 1 << 16)
     avg_pass_s = pass_ms / max(pass_n, 1) / 1e3
     bytes_per_launch = pass_bytes / max(pass_n, 1)
     flops_per_launch = bytes_per_launch / 8 * 4       # 2 FMA per element read
-    fp64_peak_tflops = 1.25                            # nominal B300 FP64 (recipe table)
     ach_tflops = flops_per_launch / avg_pass_s / 1e12
     hbm_gbs = bytes_per_launch / avg_pass_s / 1e9
     roofline = {"bound": "alu", "kernel": "k_pass (fused X^T(Xp), FP64)",
                 "achieved": ach_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                 "frac": ach_tflops / fp64_peak_tflops,
-                "peak_source": "nominal B300 FP64 1.25 TFLOP/s (recipe table); FP64 FMA probe "
-                               "measured 1.13 TFLOP/s",
+                "peak_source": "of measured: FP64 FMA rate of this GPU in this run "
+                               "(spcg_probe_fma_tflops, independent FMA chains on every SM)",
+                "peak_nominal_tflops": NOMINAL_FP64_TFLOPS,
                 # DRAM read+write bytes per launch from the ncu capture of this kernel on a
                 # 262144 x 500 operand, scaled by rows to the average launch of the solve
                 # (traffic grows with the rows read); None once the kernel changes.
                 "traffic": bytes_per_launch * K_PASS_TRAFFIC_RATIO if K_PASS_TRAFFIC_RATIO else None,
-                "hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm_gbs / hbm_peak,
-                "hbm_peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs)"
-                                    if "hbm_gbs" in peaks else
-                                    "of fallback (6.4 TB/s, no MEASURED_PEAKS.json on this host)"),
+                "hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak_gbs, "hbm_frac": hbm_gbs / hbm_peak_gbs,
+                "hbm_peak_source": hbm_src,
                 "pass_launches_per_step": pass_n / args.steps,
                 "alg_bytes_per_launch": bytes_per_launch}
-    cpu = None if args.no_cpu_baseline else cpu_baseline(w, steps=1)
     last = infos[-1]
     line = {
         "metric": "seconds to 1e-6 OLS prediction error (plain FP64 SPCG)",
@@ -636,19 +800,26 @@ def run_ours(args, w, rank, world, local_rank):
                       "refine_iters": minfos[-1].refine_iters, "restarts": minfos[-1].restarts,
                       "cond_est": minfos[-1].cond_est, "inner_prec": minfos[-1].inner_prec,
                       "grad_prec": minfos[-1].grad_prec,
-                      "pass_gbs": (mpinfo.bytes_pass / (mpinfo.pass_ms / 1e3) / 1e9)
-                      if mpinfo.pass_ms > 0 else None,
-                      "pass_hbm_frac": (mpinfo.bytes_pass / (mpinfo.pass_ms / 1e3) / 1e9
-                                        / measured_peaks().get("hbm_gbs", 6400.0))
-                      if mpinfo.pass_ms > 0 else None}},
+                      "roofline": pass_roofline(mpinfo, "float32", hbm_peak_gbs, hbm_src, None,
+                                                "k_pass<float> (Stage II on the FP32 copy)")}},
         "gpu_launches": launches,
         "roofline": roofline,
         "e2e": {"value": float(np.median(t_e2e)) / 1e3, "unit": "s",
                 "h2d_bytes_per_step": int(Xh.numel() * 8 + Yh.numel() * 8),
                 "d2h_bytes_per_step": int(d * 8)},
         "clocks": clk.summary(),
-        "cpu_baseline": cpu,
     }
+    del Xh, Yh
+    # the metric's comparisons at the other workloads (one GPU only)
+    if world == 1 and not args.headline_only:
+        for key in ("c3", "c4", "c5"):
+            fn = {"c3": run_forms, "c4": run_batched, "c5": run_learned}[key]
+            try:
+                line[key] = fn(args, WORKLOADS[key])
+            except Exception as e:   # a failed extra must not lose the headline line
+                line[key] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
+    line["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline(w, X, Y)
     print(json.dumps(line), flush=True)
 
 
@@ -660,6 +831,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the nested c3/c4/c5 comparisons of the default run")
     ap.add_argument("--kernel", default=None, choices=[None, "pass", "sketch"],
                     help="time one kernel alone instead of the solve")
     ap.add_argument("--rows", type=int, default=1 << 18)
@@ -682,11 +855,11 @@ def main():
     elif args.kernel == "sketch":
         run_sketch_only(args, w, local_rank)
     elif args.impl == "ours" and args.workload == "c3":
-        run_forms(args, w)
+        print_nested(args, w, run_forms(args, w), "bf16/f32/f64")
     elif args.impl == "ours" and args.workload == "c4":
-        run_batched(args, w)
+        print_nested(args, w, run_batched(args, w), "f32 (compensated) / f64 scalars")
     elif args.impl == "ours" and args.workload == "c5":
-        run_learned(args, w)
+        print_nested(args, w, run_learned(args, w), "f64")
     elif args.impl == "reference":
         run_reference(args, w, rank, world)
     else:

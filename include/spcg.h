@@ -120,6 +120,11 @@ typedef struct {
                                iterations, SPCG_INNER_*; 0 = automatic        */
   int32_t grad_prec;        /* SPCG_PREC_MIXED only: arithmetic of the true
                                gradients, SPCG_GRAD_*; 0 = automatic          */
+  int64_t max_workspace_bytes; /* cap on the device memory the context may hold
+                               (its workspace, without the caller's X, Y and
+                               beta); an allocation by spcg_create or
+                               spcg_sketch that would pass it fails with
+                               SPCG_E_OOM before any cudaMalloc; 0 = no cap   */
 } spcg_opts;
 
 /* Stage II operand of the mixed path (spcg_opts.inner_prec, spcg_info.inner_prec).
@@ -167,6 +172,12 @@ typedef struct {
                                used by Stage II; 0 on the FP64 path            */
   int32_t grad_prec;        /* SPCG_GRAD_F64 or SPCG_GRAD_DF: the arithmetic of
                                the true gradients of Stage II                  */
+  /* The fused passes split by operand: [0] FP64 rows, [1] FP32 rows, [2] BF16
+   * rows, [3] the double-FP32 pair (8 bytes per element).  Times only when
+   * spcg_opts.profile = 1, else 0. */
+  double pass_ms_by_op[4];
+  uint64_t bytes_by_op[4];
+  int32_t launches_by_op[4];
 } spcg_info;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -201,7 +212,8 @@ spcg_status spcg_tuned_schedule(int64_t N, int32_t d, spcg_schedule* out);
  *   stream cudaStream_t for all work of this context (NULL = default stream).
  *   opts   NULL for defaults.
  *   out    receives the context (set to NULL on failure).
- * Errors: SPCG_E_INVALID_ARG, SPCG_E_OOM, SPCG_E_CUDA.
+ * Errors: SPCG_E_INVALID_ARG, SPCG_E_OOM (a device allocation failed, or the
+ * workspace would pass opts->max_workspace_bytes), SPCG_E_CUDA.
  */
 spcg_status spcg_create(const double* X, const double* Y, int64_t N, int32_t d,
                         int64_t ldx, void* stream, const spcg_opts* opts,
@@ -220,8 +232,10 @@ void spcg_destroy(spcg_ctx* ctx);
  * The random draws (D, P, pi, I-hat) are Philox4x32-10 / Feistel
  * permutations keyed by seed, identical to spcg_feistel / spcg_signs.
  * sched NULL = spcg_default_schedule(N, d).  The schedule is copied.
- * Errors: SPCG_E_INVALID_ARG (schedule), SPCG_E_OOM, SPCG_E_CUDA,
- * SPCG_E_BREAKDOWN (R has a zero or non-finite diagonal entry).
+ * Errors: SPCG_E_INVALID_ARG (schedule), SPCG_E_OOM (a device allocation
+ * failed or would pass spcg_opts.max_workspace_bytes), SPCG_E_CUDA,
+ * SPCG_E_BREAKDOWN (X or Y holds an Inf or a NaN, found by the column maxima
+ * of the fixed-point scales; or R has a zero or non-finite diagonal entry).
  */
 spcg_status spcg_sketch(spcg_ctx* ctx, uint64_t seed, const spcg_schedule* sched);
 
@@ -254,6 +268,26 @@ spcg_status spcg_refine(spcg_ctx* ctx, double tol, int32_t max_iters,
  */
 spcg_status spcg_solve(spcg_ctx* ctx, uint64_t seed, const spcg_schedule* sched,
                        double* beta, spcg_info* info);
+
+/*
+ * Algorithm 1 end to end from HOST memory: copies X and Y to the device,
+ * solves as spcg_solve, copies beta back.  For callers that hold the problem
+ * in host memory and want one call; the copies are part of the call.
+ *   X      host, N x d row-major FP64, leading dimension ldx >= d (page-locked
+ *          memory, e.g. cudaHostAlloc, makes the copy run at full link speed)
+ *   Y      host, N FP64
+ *   sched  NULL = spcg_default_schedule(N, d); opts NULL = defaults
+ *   stream cudaStream_t for the copies and the solve (NULL = default stream)
+ *   beta   host, d FP64 output (the last iterate when SPCG_E_NOT_CONVERGED)
+ *   info   host, may be NULL
+ * Allocates device copies of X (N x d, rows padded to an even count), Y and
+ * beta plus a context, and frees all of it before returning; synchronises
+ * `stream`.  Errors: SPCG_E_INVALID_ARG, SPCG_E_OOM, SPCG_E_CUDA and those of
+ * spcg_solve.
+ */
+spcg_status spcg_solve_host(const double* X, const double* Y, int64_t N, int32_t d, int64_t ldx,
+                            uint64_t seed, const spcg_schedule* sched, const spcg_opts* opts,
+                            void* stream, double* beta, spcg_info* info);
 
 /* ----- Lower-level entry points (same kernels; for parity checks) ----- */
 
@@ -368,6 +402,20 @@ spcg_status spcg_split_f32(const double* X, int64_t N, int32_t d, int64_t ldx, f
  */
 spcg_status spcg_gram_apply_noalloc(const double* A, int64_t m, int32_t d, int64_t lda,
                                     const double* p, double* w, void* stream);
+
+/*
+ * Measurement helper (the paper has no counterpart): the fused multiply-add
+ * rate of this GPU for one arithmetic type, measured by a kernel that does
+ * nothing but independent FMA chains on every SM, timed with CUDA events on
+ * `stream` after a warm-up launch.  The plain FP64 fused pass is bound by FP64
+ * FMA issue, so this measured rate is its roofline denominator.
+ *   dtype       0 = FP64, 1 = FP32
+ *   iters       FMA steps per chain (about 2^16 takes a few milliseconds)
+ *   tflops_out  host: 2 x FMAs / elapsed seconds / 1e12
+ * Synchronises `stream`.  Errors: SPCG_E_INVALID_ARG (dtype, iters < 1, NULL
+ * output), SPCG_E_CUDA.
+ */
+spcg_status spcg_probe_fma_tflops(int32_t dtype, int32_t iters, double* tflops_out, void* stream);
 
 /* ----- Batched solver: many independent FP32 problems, one persistent kernel ----- */
 

@@ -10,7 +10,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libspcg.so")
-SOURCES = ["rng.cu", "fwht.cu", "qr.cu", "pcg.cu", "condest.cu", "api.cu", "noalloc.cu", "countsketch.cu", "mlp.cu", "batched.cu"]
+SOURCES = ["rng.cu", "fwht.cu", "qr.cu", "pcg.cu", "condest.cu", "api.cu", "noalloc.cu", "countsketch.cu", "mlp.cu", "batched.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

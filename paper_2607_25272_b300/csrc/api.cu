@@ -13,17 +13,34 @@ spcg_status from_cuda(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? SPCG_E_OOM : SPCG_E_CUDA;
 }
 
+// Device allocations of a context go through dalloc/dfree, which keep the
+// context's workspace total; with spcg_opts.max_workspace_bytes > 0 an
+// allocation that would take the total past the cap fails with SPCG_E_OOM
+// before cudaMalloc is called.
 template <typename T>
-static spcg_status dalloc(T** p, size_t count) {
+static spcg_status dalloc(spcg_ctx* c, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  SPCG_CK(cudaMalloc((void**)p, count * sizeof(T)));
+  const size_t bytes = count * sizeof(T);
+  if (c->opts.max_workspace_bytes > 0 &&
+      c->ws_bytes + bytes > (size_t)c->opts.max_workspace_bytes)
+    return SPCG_E_OOM;
+  SPCG_CK(cudaMalloc((void**)p, bytes));
+  c->ws_sizes[(const void*)*p] = bytes;
+  c->ws_bytes += bytes;
   return SPCG_OK;
 }
 
 template <typename T>
-static void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
+static void dfree(spcg_ctx* c, T*& p) {
+  if (p) {
+    auto it = c->ws_sizes.find((const void*)p);
+    if (it != c->ws_sizes.end()) {
+      c->ws_bytes -= it->second;
+      c->ws_sizes.erase(it);
+    }
+    cudaFree((void*)p);
+  }
   p = nullptr;
 }
 
@@ -58,7 +75,7 @@ static spcg_status validate_schedule(const spcg_schedule& s, int64_t N, int d) {
   return SPCG_OK;
 }
 
-spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
+spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1, int op) {
   if (c->prof_used + 2 > c->prof_cap) {
     // the stream is idle only after a sync; collect what is pending first
     SPCG_CK(cudaStreamSynchronize(c->stream));
@@ -66,10 +83,12 @@ spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
     if (c->prof_cap == 0) {
       c->prof_cap = 512;
       c->prof_ev = (cudaEvent_t*)calloc(c->prof_cap, sizeof(cudaEvent_t));
-      if (!c->prof_ev) return SPCG_E_OOM;
+      c->prof_op = (int*)calloc(c->prof_cap / 2, sizeof(int));
+      if (!c->prof_ev || !c->prof_op) return SPCG_E_OOM;
       for (int i = 0; i < c->prof_cap; ++i) SPCG_CK(cudaEventCreate(&c->prof_ev[i]));
     }
   }
+  c->prof_op[c->prof_used / 2] = op;
   *e0 = c->prof_ev[c->prof_used++];
   *e1 = c->prof_ev[c->prof_used++];
   return SPCG_OK;
@@ -80,9 +99,22 @@ spcg_status prof_collect(spcg_ctx* c) {
     float ms = 0.f;
     SPCG_CK(cudaEventElapsedTime(&ms, c->prof_ev[i], c->prof_ev[i + 1]));
     c->prof_ms += ms;
+    c->prof_ms_op[c->prof_op[i / 2] & 3] += ms;
   }
   c->prof_used = 0;
   return SPCG_OK;
+}
+
+// Launch and pass accounting of one solve (spcg_info).
+static void reset_accounting(spcg_ctx* c) {
+  c->n_launch = c->n_pass = 0;
+  c->pass_bytes = 0;
+  c->prof_ms = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    c->n_pass_op[k] = 0;
+    c->pass_bytes_op[k] = 0;
+    c->prof_ms_op[k] = 0.0;
+  }
 }
 
 // Read the device scalars (synchronises the stream) and map the device
@@ -241,15 +273,16 @@ static spcg_status run_refine(spcg_ctx* c, double tol, int max_iters, int max_re
   return SPCG_E_NOT_CONVERGED;
 }
 
-static void free_sketch(Sketch& s) {
-  dfree(s.AK16);
-  dfree(s.gather);
-  dfree(s.dest);
-  dfree(s.hdest);
-  dfree(s.work);
-  dfree(s.AK);
-  dfree(s.bK);
-  dfree(s.Ahat);
+static void free_sketch(spcg_ctx* c) {
+  Sketch& s = c->sk;
+  dfree(c, s.AK16);
+  dfree(c, s.gather);
+  dfree(c, s.dest);
+  dfree(c, s.hdest);
+  dfree(c, s.work);
+  dfree(c, s.AK);
+  dfree(c, s.bK);
+  dfree(c, s.Ahat);
   s.ready = false;
   s.rows_alloc = s.r_alloc = 0;
   s.work_bytes = 0;
@@ -345,7 +378,7 @@ extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, 
   // X: borrowed, or a padded copy when the row stride breaks the TMA rule
   if ((ldx * 8) % 16 != 0 || ((uintptr_t)X & 15u) != 0) {
     const int64_t ld2 = (d + 1) & ~int64_t(1);
-    if ((st = dalloc(&c->X_own, (size_t)N * ld2)) != SPCG_OK) return fail(st);
+    if ((st = dalloc(c, &c->X_own, (size_t)N * ld2)) != SPCG_OK) return fail(st);
     if (cudaMemcpy2DAsync(c->X_own, ld2 * 8, X, ldx * 8, (size_t)d * 8, N,
                           cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
       return fail(SPCG_E_CUDA);
@@ -355,7 +388,7 @@ extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, 
     c->X = X;
     c->ldx = ldx;
   }
-  if ((st = dalloc(&c->scal, 1)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &c->scal, 1)) != SPCG_OK) return fail(st);
   if (cudaMemsetAsync(c->scal, 0, sizeof(DevScalars), c->stream) != cudaSuccess)
     return fail(SPCG_E_CUDA);
   PcgBuffers& pb = c->pb;
@@ -365,32 +398,32 @@ extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, 
   pb.ldp = ni * 32;
   pb.n_red = (d + 31) / 32;
   pb.n_pre = (d + 3) / 4;
-  if ((st = dalloc(&pb.partials, (size_t)pb.grid * pb.ldp)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &pb.partials, (size_t)pb.grid * pb.ldp)) != SPCG_OK) return fail(st);
   double** vecs[] = {&pb.w, &pb.u, &pb.z, &pb.g[0], &pb.g[1], &pb.p[0], &pb.p[1], &c->beta_work};
   for (double** v : vecs) {
-    if ((st = dalloc(v, (size_t)d)) != SPCG_OK) return fail(st);
+    if ((st = dalloc(c, v, (size_t)d)) != SPCG_OK) return fail(st);
     if (cudaMemsetAsync(*v, 0, (size_t)d * 8, c->stream) != cudaSuccess) return fail(SPCG_E_CUDA);
   }
-  if ((st = dalloc(&pb.dots_pw, (size_t)pb.n_red)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&pb.dots_gz, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&pb.dots_rb, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &pb.dots_pw, (size_t)pb.n_red)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &pb.dots_gz, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &pb.dots_rb, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
   Sketch& s = c->sk;
-  if ((st = dalloc(&s.Rdiag, (size_t)d)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&s.R, (size_t)d * d)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&s.Rinv, (size_t)d * d)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&s.RinvT, (size_t)d * d)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&s.colmax, (size_t)d + 1)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&c->mlp_x, 16)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&c->mlp_y, 64)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&c->feat_part, 2 * 128)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(&s.colshift, (size_t)d + 1)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &s.Rdiag, (size_t)d)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &s.R, (size_t)d * d)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &s.Rinv, (size_t)d * d)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &s.RinvT, (size_t)d * d)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &s.colmax, (size_t)d + 1)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &c->mlp_x, 16)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &c->mlp_y, 64)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &c->feat_part, 2 * 128)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &s.colshift, (size_t)d + 1)) != SPCG_OK) return fail(st);
   if ((st = make_pass_geom(c->X, N, d, c->ldx, &c->gx)) != SPCG_OK) return fail(st);
   if (c->opts.precision != SPCG_PREC_FP64 && c->opts.precision != SPCG_PREC_MIXED)
     return fail(SPCG_E_INVALID_ARG);
   if (c->opts.precision == SPCG_PREC_MIXED) {
     c->ldxf = (d + 3) & ~int64_t(3);
-    if ((st = dalloc(&c->Xf, (size_t)N * c->ldxf)) != SPCG_OK) return fail(st);
-    if ((st = dalloc(&c->Xl, (size_t)N * c->ldxf)) != SPCG_OK) return fail(st);
+    if ((st = dalloc(c, &c->Xf, (size_t)N * c->ldxf)) != SPCG_OK) return fail(st);
+    if ((st = dalloc(c, &c->Xl, (size_t)N * c->ldxf)) != SPCG_OK) return fail(st);
     if (c->ldxf > d && (cudaMemsetAsync(c->Xf, 0, (size_t)N * c->ldxf * 4, c->stream) != cudaSuccess ||
                         cudaMemsetAsync(c->Xl, 0, (size_t)N * c->ldxf * 4, c->stream) != cudaSuccess))
       return fail(SPCG_E_CUDA);
@@ -409,39 +442,40 @@ extern "C" void spcg_destroy(spcg_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  free_sketch(c->sk);
-  dfree(c->sk.Rdiag);
-  dfree(c->sk.R);
-  dfree(c->sk.Rinv);
-  dfree(c->sk.RinvT);
-  dfree(c->sk.colmax);
-  dfree(c->mlp_x);
-  dfree(c->mlp_y);
-  dfree(c->feat_part);
-  dfree(c->sk.colshift);
+  free_sketch(c);
+  dfree(c, c->sk.Rdiag);
+  dfree(c, c->sk.R);
+  dfree(c, c->sk.Rinv);
+  dfree(c, c->sk.RinvT);
+  dfree(c, c->sk.colmax);
+  dfree(c, c->mlp_x);
+  dfree(c, c->mlp_y);
+  dfree(c, c->feat_part);
+  dfree(c, c->sk.colshift);
   PcgBuffers& pb = c->pb;
-  dfree(pb.partials);
-  dfree(pb.w);
-  dfree(pb.u);
-  dfree(pb.z);
-  dfree(pb.g[0]);
-  dfree(pb.g[1]);
-  dfree(pb.p[0]);
-  dfree(pb.p[1]);
-  dfree(pb.dots_pw);
-  dfree(pb.dots_gz);
-  dfree(pb.dots_rb);
-  dfree(c->beta_work);
-  dfree(c->scal);
-  dfree(c->X_own);
-  dfree(c->Xf);
-  dfree(c->Xl);
-  dfree(c->sk.AK16);
+  dfree(c, pb.partials);
+  dfree(c, pb.w);
+  dfree(c, pb.u);
+  dfree(c, pb.z);
+  dfree(c, pb.g[0]);
+  dfree(c, pb.g[1]);
+  dfree(c, pb.p[0]);
+  dfree(c, pb.p[1]);
+  dfree(c, pb.dots_pw);
+  dfree(c, pb.dots_gz);
+  dfree(c, pb.dots_rb);
+  dfree(c, c->beta_work);
+  dfree(c, c->scal);
+  dfree(c, c->X_own);
+  dfree(c, c->Xf);
+  dfree(c, c->Xl);
+  dfree(c, c->sk.AK16);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (int i = 0; i < c->prof_cap; ++i)
     if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
   free(c->prof_ev);
+  free(c->prof_op);
   delete c;
 }
 
@@ -458,12 +492,12 @@ extern "C" spcg_status spcg_sketch(spcg_ctx* c, uint64_t seed, const spcg_schedu
   const int nbits = ilog2(n_pad);
   const int64_t mK = sc.K > 0 ? sc.m[sc.K - 1] : 0;
   if (s.n_pad != n_pad) {
-    dfree(s.gather);
-    dfree(s.dest);
-    dfree(s.hdest);
-    SPCG_TRY(dalloc(&s.gather, (size_t)n_pad));
-    SPCG_TRY(dalloc(&s.dest, (size_t)n_pad));
-    SPCG_TRY(dalloc(&s.hdest, (size_t)n_pad));
+    dfree(c, s.gather);
+    dfree(c, s.dest);
+    dfree(c, s.hdest);
+    SPCG_TRY(dalloc(c, &s.gather, (size_t)n_pad));
+    SPCG_TRY(dalloc(c, &s.dest, (size_t)n_pad));
+    SPCG_TRY(dalloc(c, &s.hdest, (size_t)n_pad));
     s.n_pad = n_pad;
   }
   s.nbits = nbits;
@@ -478,8 +512,8 @@ extern "C" spcg_status spcg_sketch(spcg_ctx* c, uint64_t seed, const spcg_schedu
   size_t work_bytes = multipass ? (size_t)n_pad * (d + 1) * 8 : 0;
   if (cs) work_bytes = (size_t)(mK + sc.r) * (d + 1) * 8;   // int64 buckets of S_K and S-hat
   if (work_bytes > s.work_bytes) {
-    dfree(s.work);
-    SPCG_TRY(dalloc((unsigned char**)&s.work, work_bytes));
+    dfree(c, s.work);
+    SPCG_TRY(dalloc(c, (unsigned char**)&s.work, work_bytes));
     s.work_bytes = work_bytes;
   }
   s.ldw = d + 1;
@@ -487,19 +521,19 @@ extern "C" spcg_status spcg_sketch(spcg_ctx* c, uint64_t seed, const spcg_schedu
   s.ldak16 = (d + 7) & ~int64_t(7);
   const bool mixed = (c->opts.precision == SPCG_PREC_MIXED);
   if (rows > s.rows_alloc || mixed != s.mixed) {
-    dfree(s.AK);
-    dfree(s.AK16);
-    dfree(s.bK);
+    dfree(c, s.AK);
+    dfree(c, s.AK16);
+    dfree(c, s.bK);
     s.rows_alloc = 0;
-    SPCG_TRY(dalloc(&s.bK, (size_t)rows));
-    if (mixed) SPCG_TRY(dalloc(&s.AK16, (size_t)rows * s.ldak16));
-    else SPCG_TRY(dalloc(&s.AK, (size_t)rows * s.ldak));
+    SPCG_TRY(dalloc(c, &s.bK, (size_t)rows));
+    if (mixed) SPCG_TRY(dalloc(c, &s.AK16, (size_t)rows * s.ldak16));
+    else SPCG_TRY(dalloc(c, &s.AK, (size_t)rows * s.ldak));
     s.rows_alloc = rows;
   }
   s.mixed = mixed;
   if (sc.r > s.r_alloc) {
-    dfree(s.Ahat);
-    SPCG_TRY(dalloc(&s.Ahat, (size_t)sc.r * d));
+    dfree(c, s.Ahat);
+    SPCG_TRY(dalloc(c, &s.Ahat, (size_t)sc.r * d));
     s.r_alloc = sc.r;
   }
   s.seed = seed;
@@ -553,9 +587,7 @@ extern "C" spcg_status spcg_solve(spcg_ctx* c, uint64_t seed, const spcg_schedul
                                   double* beta, spcg_info* info) {
   if (!c || !beta) return SPCG_E_INVALID_ARG;
   if (info) memset(info, 0, sizeof(*info));
-  c->n_launch = c->n_pass = 0;
-  c->pass_bytes = 0;
-  c->prof_ms = 0.0;
+  reset_accounting(c);
   SPCG_CK(cudaEventRecord(c->ev[0], c->stream));
   SPCG_TRY(spcg_sketch(c, seed, sched));
   if (c->opts.precision == SPCG_PREC_MIXED) SPCG_TRY(launch_to_f32(c));
@@ -577,6 +609,11 @@ extern "C" spcg_status spcg_solve(spcg_ctx* c, uint64_t seed, const spcg_schedul
     info->pass_launches = (int32_t)c->n_pass;
     info->launches = (int32_t)c->n_launch;
     info->pass_ms = c->prof_ms;
+    for (int k = 0; k < 4; ++k) {
+      info->pass_ms_by_op[k] = c->prof_ms_op[k];
+      info->bytes_by_op[k] = c->pass_bytes_op[k];
+      info->launches_by_op[k] = (int32_t)c->n_pass_op[k];
+    }
     for (int i = 0; i < sc.K; ++i) info->stage_iters[i] = sc.a[i];
     info->refine_iters = rr.iters;
     info->restarts = rr.restarts;
@@ -596,6 +633,46 @@ extern "C" spcg_status spcg_solve(spcg_ctx* c, uint64_t seed, const spcg_schedul
     info->ms_refine = ms;
   }
   return st;
+}
+
+extern "C" spcg_status spcg_solve_host(const double* X, const double* Y, int64_t N, int32_t d,
+                                       int64_t ldx, uint64_t seed, const spcg_schedule* sched,
+                                       const spcg_opts* opts, void* stream, double* beta,
+                                       spcg_info* info) {
+  if (!X || !Y || !beta || d < 1 || d > SPCG_MAX_D || N <= d || N > (int64_t(1) << 30) ||
+      ldx < d)
+    return SPCG_E_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ld = (d + 1) & ~int64_t(1);   // device rows 16-byte aligned (TMA stride rule)
+  double *Xd = nullptr, *Yd = nullptr, *bd = nullptr;
+  spcg_ctx* c = nullptr;
+  spcg_status res = SPCG_OK;
+  cudaError_t e = cudaMalloc((void**)&Xd, (size_t)N * ld * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&Yd, (size_t)N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bd, (size_t)d * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(Xd, ld * sizeof(double), X, ldx * sizeof(double), d * sizeof(double), N,
+                          cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Yd, Y, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) res = from_cuda(e);
+  if (res == SPCG_OK) res = spcg_create(Xd, Yd, N, d, ld, stream, opts, &c);
+  spcg_status solve_st = SPCG_OK;
+  if (res == SPCG_OK) {
+    solve_st = spcg_solve(c, seed, sched, bd, info);
+    // beta is copied back also when the solve did not converge (last iterate)
+    if (solve_st == SPCG_OK || solve_st == SPCG_E_NOT_CONVERGED) {
+      e = cudaMemcpyAsync(beta, bd, (size_t)d * sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) res = from_cuda(e);
+    }
+  }
+  if (c) spcg_destroy(c);
+  if (!c && res != SPCG_OK) cudaStreamSynchronize(st);   // copies may still read X, Y
+  cudaFree(Xd);
+  cudaFree(Yd);
+  cudaFree(bd);
+  return res != SPCG_OK ? res : solve_st;
 }
 
 extern "C" spcg_status spcg_export_sketch(spcg_ctx* c, int64_t row0, int64_t nrows, double* A,
@@ -770,9 +847,7 @@ static spcg_status solve_choice(spcg_ctx* c, uint64_t seed, const uint16_t* Wb, 
   spcg_schedule sc;
   SPCG_TRY(spcg_default_schedule(c->N, c->d, &sc));
   sc.tol = tol;
-  c->n_launch = c->n_pass = 0;
-  c->pass_bytes = 0;
-  c->prof_ms = 0.0;
+  reset_accounting(c);
   SPCG_CK(cudaEventRecord(c->ev[0], c->stream));
   const bool have = reuse && c->sk.ready && c->sk.seed == seed &&
                     c->sk.sched.sketch == SPCG_SKETCH_SRHT && c->sk.sched.K == sc.K &&
@@ -836,6 +911,11 @@ static spcg_status solve_choice(spcg_ctx* c, uint64_t seed, const uint16_t* Wb, 
     info->pass_launches = (int32_t)c->n_pass;
     info->launches = (int32_t)c->n_launch;
     info->pass_ms = c->prof_ms;
+    for (int k = 0; k < 4; ++k) {
+      info->pass_ms_by_op[k] = c->prof_ms_op[k];
+      info->bytes_by_op[k] = c->pass_bytes_op[k];
+      info->launches_by_op[k] = (int32_t)c->n_pass_op[k];
+    }
     float ms;
     cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
     info->ms_sketch = ms;

@@ -25,6 +25,8 @@
 // S-hat X = sqrt(N'/r) H D P X' [I-hat] = H' D P X' [I-hat] / sqrt(r).
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -103,13 +105,17 @@ __global__ void __launch_bounds__(256) k_colmax(const double* __restrict__ X, in
 }
 
 // s_c = 61 - n - E_c with 2^{E_c} <= max_c < 2^{E_c+1}: every partial sum of
-// N' <= 2^n terms stays below 2^62 in magnitude.
+// N' <= 2^n terms stays below 2^62 in magnitude.  A column holding an Inf or
+// a NaN (the largest bit pattern then has the all-ones exponent) has no such
+// scale: the device status becomes BREAKDOWN and the column gets shift 0, so
+// the transform still only moves values (no shift or index depends on them).
 __global__ void k_colscale(const unsigned long long* __restrict__ colmax, int C, int nbits,
-                           int* __restrict__ shift) {
+                           int* __restrict__ shift, int* __restrict__ status) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
     const unsigned long long b = colmax[c];
     const int e = (int)((b >> 52) & 0x7FF);
-    shift[c] = (e == 0) ? 0 : 61 - nbits - (e - 1023);
+    if (e == 0x7FF) atomicExch(status, DEV_BREAKDOWN);
+    shift[c] = (e == 0 || e == 0x7FF) ? 0 : 61 - nbits - (e - 1023);
   }
 }
 
@@ -348,7 +354,8 @@ spcg_status launch_colscales(spcg_ctx* c) {
   if (cg < 1) cg = 1;
   k_colmax<<<cg, 256, 0, c->stream>>>(c->X, c->ldx, c->Y, c->N, c->d, s.colmax);
   SPCG_CK(cudaGetLastError());
-  k_colscale<<<(C + 255) / 256, 256, 0, c->stream>>>(s.colmax, C, s.nbits, s.colshift);
+  k_colscale<<<(C + 255) / 256, 256, 0, c->stream>>>(s.colmax, C, s.nbits, s.colshift,
+                                                 &c->scal->status);
   SPCG_CK(cudaGetLastError());
   c->n_launch += 2;
   return SPCG_OK;
@@ -500,14 +507,21 @@ __global__ void __launch_bounds__(256) k_to_f32(const double* __restrict__ X, in
   }
 }
 
-// Resident CTAs per SM of k_to_f32, computed once (thread-safe static).
+// Resident CTAs per SM of k_to_f32 on the current device, computed once per
+// device (the answer depends on the device's limits; a racing first call on
+// two threads computes the same value twice).
 static int to_f32_blocks_per_sm() {
-  static const int per_sm = []() {
-    int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_to_f32, 256, 0) != cudaSuccess) v = 1;
-    return v > 0 ? v : 1;
-  }();
-  return per_sm;
+  static std::atomic<int> per_dev[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int v = per_dev[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_to_f32, 256, 0) != cudaSuccess || v < 1) {
+    (void)cudaGetLastError();
+    return 1;
+  }
+  per_dev[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 spcg_status launch_to_f32(spcg_ctx* c) {

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <unordered_map>
+
 #include "../../include/spcg.h"
 
 namespace spcg {
@@ -22,6 +24,9 @@ struct DevScalars {
 
 // Element types of a fused-pass operand.
 enum : int { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2 };
+// Operand kinds of the pass accounting (spcg_info.*_by_op): the three
+// element types and the double-FP32 pair.
+enum : int { OP_F64 = 0, OP_F32 = 1, OP_BF16 = 2, OP_PAIR = 3 };
 
 // Geometry of the fused pass over one operand.
 struct PassGeom {
@@ -128,10 +133,18 @@ struct spcg_ctx {
   int64_t n_launch = 0;
   int64_t n_pass = 0;
   uint64_t pass_bytes = 0;
+  // the same per operand kind (OP_*: FP64, FP32, BF16 rows, double-FP32 pair)
+  int64_t n_pass_op[4] = {0, 0, 0, 0};
+  uint64_t pass_bytes_op[4] = {0, 0, 0, 0};
+  double prof_ms_op[4] = {0.0, 0.0, 0.0, 0.0};
+  int* prof_op = nullptr;           // operand kind of each event pair
   cudaEvent_t* prof_ev = nullptr;   // pairs around fused-pass launches
   int prof_cap = 0;
   int prof_used = 0;
   double prof_ms = 0.0;
+  // device workspace of this context (dalloc/dfree in api.cu)
+  size_t ws_bytes = 0;
+  std::unordered_map<const void*, size_t> ws_sizes;
 };
 
 namespace spcg {
@@ -172,7 +185,7 @@ spcg_status launch_precond_T(spcg_ctx* c, int iter_mode, int cur, int pp, int gp
 spcg_status launch_precond(spcg_ctx* c, int cur, const double* beta);
 spcg_status launch_check(spcg_ctx* c, double tau);
 spcg_status launch_reset_flags(spcg_ctx* c);
-spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1);
+spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1, int op);
 spcg_status prof_collect(spcg_ctx* c);   // after a stream sync
 spcg_status pass_gram_plain(spcg_ctx* c, const PassGeom& g, const double* p);
 spcg_status make_pass_geom_df(const float* Xh, const float* Xl, int64_t m, int d, int64_t lda,

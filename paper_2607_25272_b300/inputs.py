@@ -110,3 +110,26 @@ def svd_problem_device(N, d, kappa, sigma, seed=1, leverage_df=None, device="cud
     uty = G.T @ Y
     del G
     return X.contiguous(), Y, beta, uty, s, V
+
+
+def scaled_columns_problem_device(N, d, lo, hi, sigma, seed=1, device="cuda",
+                                  dtype=None):
+    """The scaled_columns_problem recipe drawn on a CUDA device with torch
+    (same construction, a different random stream): X_ij iid N(0,1) times
+    per-column scales 10^U(log10 lo, log10 hi), beta iid N(0,1),
+    Y = X beta + sigma zeta, formed in FP64 and returned in `dtype`
+    (default float64)."""
+    import math
+
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = torch.float64
+    c = 10.0 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo)) *
+                 torch.rand(d, dtype=f64, device=device, generator=g))
+    X = torch.randn((N, d), dtype=f64, device=device, generator=g) * c[None, :]
+    beta = torch.randn(d, dtype=f64, device=device, generator=g)
+    Y = X @ beta + sigma * torch.randn(N, dtype=f64, device=device, generator=g)
+    if dtype is not None:
+        X, Y = X.to(dtype), Y.to(dtype)
+    return X, Y, beta

@@ -75,13 +75,28 @@ def test_invalid_arguments_rejected_before_any_cuda_call():
     assert L.spcg_split_f32(f16, 10, 5, 4, f16, f16, 6, None) == S.SPCG_E_INVALID_ARG    # ldx < d
     assert L.spcg_split_f32(f16, -1, 5, 6, f16, f16, 6, None) == S.SPCG_E_INVALID_ARG
     assert L.spcg_split_f32(None, 0, 5, 6, None, None, 6, None) == S.SPCG_OK             # N = 0
+    # the allocation-free pass checks its arguments before any CUDA call
+    assert L.spcg_gram_apply_noalloc(f16, 10, 0, 10, f16, f16, None) == S.SPCG_E_INVALID_ARG   # d = 0
+    assert L.spcg_gram_apply_noalloc(f16, 10, 1025, 1026, f16, f16,
+                                     None) == S.SPCG_E_INVALID_ARG                          # d > 1024
+    assert L.spcg_gram_apply_noalloc(f16, 10, 8, 7, f16, f16, None) == S.SPCG_E_INVALID_ARG    # lda < d
+    assert L.spcg_gram_apply_noalloc(f16, 10, 8, 8, None, f16, None) == S.SPCG_E_INVALID_ARG   # p NULL
+    assert L.spcg_gram_apply_noalloc(f16, 10, 8, 8, f16, None, None) == S.SPCG_E_INVALID_ARG   # w NULL
+    assert L.spcg_gram_apply_noalloc(None, 10, 8, 8, f16, f16, None) == S.SPCG_E_INVALID_ARG   # A NULL
+    assert L.spcg_gram_apply_noalloc(f16, -1, 8, 8, f16, f16, None) == S.SPCG_E_INVALID_ARG    # m < 0
+    # the FMA probe: bad type, no iterations, NULL output
+    out_d = ctypes.c_double(0.0)
+    assert L.spcg_probe_fma_tflops(2, 10, ctypes.byref(out_d), None) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_probe_fma_tflops(0, 0, ctypes.byref(out_d), None) == S.SPCG_E_INVALID_ARG
+    assert L.spcg_probe_fma_tflops(0, 10, None, None) == S.SPCG_E_INVALID_ARG
     L.spcg_destroy(None)   # no-op
 
 
 def test_struct_layouts_match_header_sizes():
     # spcg_schedule: int32 K, int64 m[40], int32 a[40], int64 r, double tol, 2 x int32
     assert ctypes.sizeof(S.Schedule) == 8 + 8 * 40 + 4 * 40 + 8 + 8 + 8 + 8
-    assert ctypes.sizeof(S.Opts) == 4 + 4 + 8 + 16
+    # spcg_opts: int32 precision, grid_ctas; int64 spin_budget; 4 x int32; int64 cap
+    assert ctypes.sizeof(S.Opts) == 4 + 4 + 8 + 16 + 8
 
 
 def test_struct_layouts_match_a_c_compiler(tmp_path):

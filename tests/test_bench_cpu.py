@@ -1,0 +1,33 @@
+"""Host-side checks of bench.py's oracle arm: the phase-by-phase run of the
+oracle's SPCG solve (the reference arm splits one full-size solve over its
+timed steps at these boundaries) gives the same beta as one call of the
+oracle's own spcg, bit for bit, and every phase runs exactly once."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from oracle.spcg import spcg as oracle_spcg  # noqa: E402
+from paper_2607_25272_b300.inputs import svd_problem  # noqa: E402
+
+
+def test_phase_split_equals_one_oracle_call():
+    X, Y, _ = svd_problem(5000, 20, 1e4, 0.1, seed=3)
+    phases = bench.oracle_phases(X, Y, 7, 1e-6)
+    out = None
+    for ph in phases:
+        out = ph()
+    ref = oracle_spcg(X, Y, seed=7, tol=1e-6)["beta"]
+    assert np.array_equal(out, ref)
+
+
+def test_phase_groups_cover_every_phase_once():
+    for n_phases in (3, 11, 15):
+        for K in (1, 2, 5, 11, 20):
+            ph = list(range(n_phases))
+            groups = bench.phase_groups(ph, K)
+            assert sum(groups, []) == ph and len(groups) == K

@@ -128,4 +128,33 @@ def test_trained_model_beats_the_paper_schedule_on_held_out_problems():
         learned += il.ms_stages + il.ms_refine
         paper += ip.ms_stages + ip.ms_refine
         s.close()
-    assert learned < paper
+    # a stated margin, not just "faster": at least 1.1x over the 16 problems
+    assert paper >= 1.1 * learned, (paper, learned)
+
+
+def test_learned_schedule_at_full_size():
+    """The learned-schedule workload at its full size (N = 2^23, d = 256,
+    kappa = 1e4, sigma = 0.5), in the configuration bench.py times: the
+    model's schedule and the paper's fallback both meet 1e-6.  At this size
+    the host oracle is replaced by a property that holds at any size: for
+    X = U diag(s) V^T with orthonormal U the OLS estimator is
+    V diag(1/s) U^T Y, and ||X v|| = ||diag(s) V^T v||."""
+    from paper_2607_25272_b300.inputs import svd_problem_device
+    Wb, norm = SM.load()
+    if Wb is None:
+        pytest.skip("no trained weights")
+    X, Y, _, uty, sv, V = svd_problem_device(1 << 23, 256, 1e4, 0.5, seed=1, device="cuda")
+    b_ols = V @ (uty / sv)
+
+    def rel_err(beta):
+        return float(torch.linalg.norm(sv * (V.T @ (beta - b_ols))) /
+                     torch.linalg.norm(sv * (V.T @ b_ols)))
+
+    s = S.Solver(X, Y)
+    for W in (Wb, None):
+        beta, info, choice, st = s.solve_learned(1, W, norm, tol=1e-6)
+        assert st == S.SPCG_OK and info.converged == 1
+        if W is None:
+            assert choice == SM.PAPER_CANDIDATE
+        assert rel_err(beta) <= 1e-6
+    s.close()
