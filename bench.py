@@ -124,6 +124,17 @@ def pass_roofline(info, op, peak_gbs, peak_source, traffic_ratio, kernel):
             "launches_per_step": n, "alg_bytes_per_launch": per_launch}
 
 
+def host_mem_available():
+    """Available host memory in bytes (/proc/meminfo), 0 if unknown."""
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
 def hbm_peak():
     peaks = measured_peaks()
     if "hbm_gbs" in peaks:
@@ -188,11 +199,7 @@ def run_forms(args, w):
     # end to end through the public API from pinned host buffers, when the
     # host can hold a pinned copy of X (33.6 GB)
     e2e = None
-    try:
-        import psutil
-        avail = psutil.virtual_memory().available
-    except ImportError:
-        avail = 0
+    avail = host_mem_available()
     nbytes = N * d * 8 + N * 8
     if avail > 3 * nbytes:
         Xh = Xd.cpu().pin_memory()
@@ -619,7 +626,11 @@ def run_sketch_only(args, w, local_rank):
     m, d = args.rows, w["d"]
     X = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g)
     Y = torch.randn(m, dtype=torch.float64, device=dev, generator=g)
-    s = S.Solver(X, Y)
+    o = S.Opts()
+    o.fwht_tile = args.fwht_tile
+    o.fwht_first_levels = args.fwht_first
+    o.qr_by_column = args.qr_by_column
+    s = S.Solver(X, Y, o)
     sc = S.spcg_default_schedule(m, d)
     for _ in range(args.warmup):
         s.sketch(1, sc)
@@ -632,7 +643,8 @@ def run_sketch_only(args, w, local_rank):
         s.sketch(1, sc)
     e1.record(stream)
     torch.cuda.synchronize()
-    print(json.dumps({"kernel": "spcg_sketch", "rows": m, "d": d,
+    print(json.dumps({"kernel": "spcg_sketch", "rows": m, "d": d, "fwht_tile": args.fwht_tile,
+                      "fwht_first_levels": args.fwht_first, "qr_by_column": args.qr_by_column,
                       "ms_per_call": e0.elapsed_time(e1) / args.steps}), flush=True)
     s.close()
 
@@ -840,6 +852,12 @@ def main():
     ap.add_argument("--ncu-region", default=None, choices=[None, "plain", "mixed"],
                     help="bracket the timed solves of this form with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
+    ap.add_argument("--fwht-tile", type=int, default=0,
+                    help="spcg_opts.fwht_tile for --kernel sketch (0 default, 1, 2, 3)")
+    ap.add_argument("--fwht-first", type=int, default=0,
+                    help="spcg_opts.fwht_first_levels for --kernel sketch")
+    ap.add_argument("--qr-by-column", type=int, default=0,
+                    help="spcg_opts.qr_by_column for --kernel sketch")
     ap.add_argument("--pass-dtype", default="float64",
                     choices=["float64", "float32", "bfloat16", "pair"])
     args = ap.parse_args()

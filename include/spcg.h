@@ -125,6 +125,17 @@ typedef struct {
                                beta); an allocation by spcg_create or
                                spcg_sketch that would pass it fails with
                                SPCG_E_OOM before any cudaMalloc; 0 = no cap   */
+  int32_t qr_by_column;     /* 1 = factor the preconditioner sketch with one
+                               launch per Householder step instead of the
+                               blocked cooperative QR (same factorisation,
+                               slower; for comparison)                         */
+  int32_t fwht_tile;        /* transform passes of 9..12 levels: 0 = default
+                               (1), 1 = 128 KB tiles, one CTA per SM, 2 = 64 KB
+                               tiles, two CTAs per SM (9 or 10 levels; others
+                               as 1), 3 = the per-round pass kernel           */
+  int32_t fwht_first_levels; /* levels of the first of two transform passes;
+                               0 = split evenly                               */
+  int32_t reserved;         /* set to 0                                         */
 } spcg_opts;
 
 /* Stage II operand of the mixed path (spcg_opts.inner_prec, spcg_info.inner_prec).

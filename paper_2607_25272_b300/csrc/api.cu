@@ -44,6 +44,19 @@ static void dfree(spcg_ctx* c, T*& p) {
   p = nullptr;
 }
 
+// Scratch of the cooperative QR (launch_precond_factor): one CTA per SM at
+// most, panels of kQrPanel columns.
+static spcg_status qr_alloc(spcg_ctx* c) {
+  Sketch& s = c->sk;
+  const int d = c->d, G = c->num_sms;
+  SPCG_TRY(dalloc(c, &s.qr_vdiag, (size_t)d));
+  SPCG_TRY(dalloc(c, &s.qr_red, (size_t)2 * G * 2 * kQrPanel));
+  SPCG_TRY(dalloc(c, &s.qr_wp, (size_t)G * kQrPanel * d));
+  SPCG_TRY(dalloc(c, &s.qr_wt, (size_t)kQrPanel * d));
+  SPCG_TRY(dalloc(c, &s.qr_bar, (size_t)2));
+  return SPCG_OK;
+}
+
 static int64_t next_pow2(int64_t n) {
   int64_t p = 1;
   while (p < n) p <<= 1;
@@ -138,10 +151,8 @@ static spcg_status start_sequence(spcg_ctx* c, const PassGeom& g, const double* 
                                   double* beta, int& cur, bool df = false) {
   if (df) SPCG_TRY(pass_resid_df(c, c->gxdf, c->tml, b, beta));
   else SPCG_TRY(pass_resid(c, g, b, beta));
-  SPCG_TRY(launch_reduce(c, c->pb.g[cur], nullptr));
-  SPCG_TRY(launch_precond_T(c, 0, cur, 0, 0, beta));
+  SPCG_TRY(launch_dspace(c, 0, cur, 0, 0, beta));   // g, u = R^{-T} g, z, dots
   cur ^= 1;
-  SPCG_TRY(launch_precond(c, cur, beta));
   return SPCG_OK;
 }
 
@@ -152,17 +163,16 @@ struct Operand {
   const CUtensorMap* tml;
 };
 
-// One PCG iteration (four launches) after start_sequence or a previous one.
+// One PCG iteration (two launches: the fused pass and the d-space kernel)
+// after start_sequence or a previous one.
 static spcg_status iteration(spcg_ctx* c, const Operand& op, double* beta, int& cur, int& pp,
                              int& gp, int start, int check, double tau) {
   if (op.tml) SPCG_TRY(pass_gram_iter_df(c, *op.g, *op.tml, pp, gp, start, check, tau));
   else SPCG_TRY(pass_gram_iter(c, *op.g, pp, gp, start, check, tau));
   pp ^= 1;
   gp ^= 1;
-  SPCG_TRY(launch_reduce(c, c->pb.w, c->pb.p[pp]));
-  SPCG_TRY(launch_precond_T(c, 1, cur, pp, gp, beta));
+  SPCG_TRY(launch_dspace(c, 1, cur, pp, gp, beta));
   cur ^= 1;
-  SPCG_TRY(launch_precond(c, cur, beta));
   return SPCG_OK;
 }
 
@@ -398,13 +408,15 @@ extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, 
   pb.ldp = ni * 32;
   pb.n_red = (d + 31) / 32;
   pb.n_pre = (d + 3) / 4;
+  pb.n_ds = dspace_grid(c);
   if ((st = dalloc(c, &pb.partials, (size_t)pb.grid * pb.ldp)) != SPCG_OK) return fail(st);
   double** vecs[] = {&pb.w, &pb.u, &pb.z, &pb.g[0], &pb.g[1], &pb.p[0], &pb.p[1], &c->beta_work};
   for (double** v : vecs) {
     if ((st = dalloc(c, v, (size_t)d)) != SPCG_OK) return fail(st);
     if (cudaMemsetAsync(*v, 0, (size_t)d * 8, c->stream) != cudaSuccess) return fail(SPCG_E_CUDA);
   }
-  if ((st = dalloc(c, &pb.dots_pw, (size_t)pb.n_red)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &pb.dots_pw, (size_t)(pb.n_pre > pb.n_red ? pb.n_pre : pb.n_red))) != SPCG_OK)
+    return fail(st);
   if ((st = dalloc(c, &pb.dots_gz, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
   if ((st = dalloc(c, &pb.dots_rb, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
   Sketch& s = c->sk;
@@ -413,12 +425,16 @@ extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, 
   if ((st = dalloc(c, &s.Rinv, (size_t)d * d)) != SPCG_OK) return fail(st);
   if ((st = dalloc(c, &s.RinvT, (size_t)d * d)) != SPCG_OK) return fail(st);
   if ((st = dalloc(c, &s.colmax, (size_t)d + 1)) != SPCG_OK) return fail(st);
+  if ((st = qr_alloc(c)) != SPCG_OK) return fail(st);
   if ((st = dalloc(c, &c->mlp_x, 16)) != SPCG_OK) return fail(st);
   if ((st = dalloc(c, &c->mlp_y, 64)) != SPCG_OK) return fail(st);
   if ((st = dalloc(c, &c->feat_part, 2 * 128)) != SPCG_OK) return fail(st);
   if ((st = dalloc(c, &s.colshift, (size_t)d + 1)) != SPCG_OK) return fail(st);
   if ((st = make_pass_geom(c->X, N, d, c->ldx, &c->gx)) != SPCG_OK) return fail(st);
   if (c->opts.precision != SPCG_PREC_FP64 && c->opts.precision != SPCG_PREC_MIXED)
+    return fail(SPCG_E_INVALID_ARG);
+  if (c->opts.fwht_tile < 0 || c->opts.fwht_tile > 3 || c->opts.fwht_first_levels < 0 ||
+      c->opts.fwht_first_levels > 12 || c->opts.max_workspace_bytes < 0)
     return fail(SPCG_E_INVALID_ARG);
   if (c->opts.precision == SPCG_PREC_MIXED) {
     c->ldxf = (d + 3) & ~int64_t(3);
@@ -448,6 +464,11 @@ extern "C" void spcg_destroy(spcg_ctx* c) {
   dfree(c, c->sk.Rinv);
   dfree(c, c->sk.RinvT);
   dfree(c, c->sk.colmax);
+  dfree(c, c->sk.qr_vdiag);
+  dfree(c, c->sk.qr_red);
+  dfree(c, c->sk.qr_wp);
+  dfree(c, c->sk.qr_wt);
+  dfree(c, c->sk.qr_bar);
   dfree(c, c->mlp_x);
   dfree(c, c->mlp_y);
   dfree(c, c->feat_part);

@@ -103,4 +103,46 @@ __device__ __forceinline__ float warp_allsum(float v) {
   return v;
 }
 
+// ---------------------------------------------------------------------------
+// Grid barrier of a cooperative launch (every CTA of the grid is resident).
+// bar[0] counts arrivals, bar[1] is the generation.  The last CTA to arrive
+// resets the count and advances the generation; the others wait until the
+// generation changes, at most `spin` clock cycles.  Returns false when the
+// wait expired: the status word is set to DEV_TIMEOUT and the CTA must leave
+// (the other CTAs then time out at their next barrier).  Called by every
+// thread of the CTA; *s_fail is a shared flag, 0 at kernel start.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_gpu_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, int* status, long long spin,
+                                                  int* s_fail) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = ld_acquire_gpu_u32(bar + 1);
+    __threadfence();
+    const unsigned prev = atomicAdd(bar, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_gpu_u32(bar + 1) == g) {
+        if (clock64() - t0 > spin) {
+          atomicExch(status, DEV_TIMEOUT);
+          *s_fail = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *s_fail == 0;
+}
+
 }  // namespace spcg

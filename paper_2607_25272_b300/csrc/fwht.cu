@@ -306,6 +306,165 @@ __global__ void __launch_bounds__(512) k_fwht_pass(const FwhtArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled pass for 9..12 levels (the passes of every N' >= 2^18).  A CTA holds
+// one 128 KB tile: L = 2^LOGL rows (2^shift_lo apart) x TC adjacent columns.
+// Every thread keeps one column c for the whole pass, so the column's
+// fixed-point shift stays in a register, and owns VPT = L TC / NT values per
+// round (32 or 64 registers of int64).  Two register rounds cover the pass:
+// round 0 runs levels [0, G0) on 2^G0 consecutive tile rows, round 1 levels
+// [G0, LOGL) on rows 2^G0 apart, with one trip through shared memory between
+// them.  Tile rows are padded every 2^G0 rows so that the 64-bit accesses of a
+// half-warp fall in distinct banks in both rounds.
+// ---------------------------------------------------------------------------
+// Tile variants: V = 1, 128 KB tiles and 64 values a thread (one CTA per
+// SM); V = 2, 64 KB tiles and 32 values a thread (two CTAs per SM, so one
+// CTA's loads overlap the other's butterflies; 9 and 10 levels only).
+template <int LOGL, int V> struct TileCfg;
+template <> struct TileCfg<9, 1> { static constexpr int TC = 32, NT = 256, G0 = 6, MINB = 1; };
+template <> struct TileCfg<10, 1> { static constexpr int TC = 16, NT = 256, G0 = 6, MINB = 1; };
+template <> struct TileCfg<11, 1> { static constexpr int TC = 8, NT = 256, G0 = 6, MINB = 1; };
+template <> struct TileCfg<12, 1> { static constexpr int TC = 4, NT = 256, G0 = 6, MINB = 1; };
+template <> struct TileCfg<9, 2> { static constexpr int TC = 16, NT = 256, G0 = 5, MINB = 2; };
+template <> struct TileCfg<10, 2> { static constexpr int TC = 8, NT = 256, G0 = 5, MINB = 2; };
+
+template <int LOGL, int V>
+struct TileShape {
+  using C = TileCfg<LOGL, V>;
+  static constexpr int MINB = C::MINB;
+  static constexpr int L = 1 << LOGL, TC = C::TC, NT = C::NT, G0 = C::G0, G1 = LOGL - G0;
+  static constexpr int TPC = NT / TC;                   // threads per column
+  static constexpr int VPT = L * TC / NT;               // values per thread and round
+  static constexpr int NG1 = (1 << G0) / TPC;           // round-1 groups per thread
+  static constexpr int PAD = TC < 16 ? 16 - TC : 0;     // words per 2^G0 tile rows
+  static constexpr size_t WORDS = (size_t)L * TC + (size_t)(L >> G0) * PAD;
+  static constexpr size_t SMEM = WORDS * 8 + (size_t)L * 3 * 4;
+  static_assert(VPT == (1 << G0), "round 0 is one group per thread");
+  static_assert(NG1 * (1 << G1) == VPT, "round 1 covers the thread's values");
+  static_assert(G1 >= 1 && G1 <= G0, "levels per round");
+};
+
+template <int LOGL, int V>
+__device__ __forceinline__ int tile_word(int t, int c) {
+  using S = TileShape<LOGL, V>;
+  return t * S::TC + c + (t >> S::G0) * S::PAD;
+}
+
+template <int LOGL, int V>
+__global__ void __launch_bounds__(TileShape<LOGL, V>::NT, TileShape<LOGL, V>::MINB)
+    k_fwht_tile(const FwhtArgs a) {
+  using S = TileShape<LOGL, V>;
+  constexpr int L = S::L, TC = S::TC, G0 = S::G0, G1 = S::G1, VPT = S::VPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long long* tile = reinterpret_cast<long long*>(smem_raw);
+  int32_t* gmap = reinterpret_cast<int32_t*>(tile + S::WORDS);
+  int32_t* dmap = gmap + L;
+  int32_t* hmap = dmap + L;
+  const int tid = threadIdx.x;
+  const int64_t blk = blockIdx.x;
+  const int ct = (int)(blk % a.ncoltiles);
+  const int64_t base = blk / a.ncoltiles;
+  const int64_t low = base & ((int64_t(1) << a.shift_lo) - 1);
+  const int64_t high = base >> a.shift_lo;
+  // global row of tile row t: j0 + t * step
+  const int64_t j0 = low | (high << (a.shift_lo + LOGL));
+  const int64_t step = int64_t(1) << a.shift_lo;
+  const int c = tid % TC, r = tid / TC;
+  const int col = ct * TC + c;
+  const bool colok = col < a.C;
+  const int sh = colok ? a.shift[col] : 0;
+  if (a.first)
+    for (int t = tid; t < L; t += S::NT) gmap[t] = (int32_t)a.gather[j0 + t * step];
+  if (a.last)
+    for (int t = tid; t < L; t += S::NT) {
+      dmap[t] = a.dest[j0 + t * step];
+      hmap[t] = a.hdest[j0 + t * step];
+    }
+  __syncthreads();
+  long long v[VPT];
+  // ---- round 0: rows t = r 2^G0 + k ----
+  {
+    const int t0 = r << G0;
+    if (a.first) {
+      // column pointer and row stride of this thread's column (Y is column d)
+      const double* cp = (colok && col < a.d) ? a.X + col : a.Y;
+      const int64_t cstride = (colok && col < a.d) ? a.ldx : 1;
+      // all loads first (the raw bits held in v; sign and padding-row flags
+      // as bit masks), then the conversions
+      unsigned long long negm = 0ull, okm = 0ull;
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const uint32_t gm = (uint32_t)gmap[t0 + k];
+        const int64_t src = (int64_t)(gm & 0x7FFFFFFFu);
+        const bool ok = src < a.N;
+        negm |= (unsigned long long)(gm >> 31) << k;
+        okm |= (unsigned long long)ok << k;
+        v[k] = __double_as_longlong(__ldg(cp + (ok ? src : 0) * cstride));
+      }
+      if (!colok) okm = 0ull;
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const long long x = ((okm >> k) & 1ull) ? to_fixed(__longlong_as_double(v[k]), sh) : 0;
+        v[k] = ((negm >> k) & 1ull) ? -x : x;
+      }
+    } else {
+      const long long* wp = reinterpret_cast<const long long*>(a.W) + (colok ? col : 0);
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) v[k] = wp[(j0 + (int64_t)(t0 + k) * step) * a.ldw];
+      if (!colok)
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) v[k] = 0;
+    }
+    bfly<G0>(v);
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) tile[tile_word<LOGL, V>(t0 + k, c)] = v[k];
+  }
+  __syncthreads();
+  // ---- round 1: NG1 groups, rows t = gi + k 2^G0 with gi < 2^G0 ----
+#pragma unroll
+  for (int m = 0; m < S::NG1; ++m) {
+    const int gi = r + m * S::TPC;
+    long long u[1 << G1];
+#pragma unroll
+    for (int k = 0; k < (1 << G1); ++k) u[k] = tile[tile_word<LOGL, V>(gi + (k << G0), c)];
+    bfly<G1>(u);
+#pragma unroll
+    for (int k = 0; k < (1 << G1); ++k) {
+      const int t = gi + (k << G0);
+      if (!colok) continue;
+      if (!a.last) {
+        reinterpret_cast<long long*>(a.W)[(j0 + (int64_t)t * step) * a.ldw + col] = u[k];
+      } else {
+        const int32_t dst = dmap[t], hd = hmap[t];
+        if (dst >= 0 || hd >= 0) {
+          const double z = from_fixed(u[k], sh);
+          if (dst >= 0) {
+            if (col < a.d) {
+              if (a.AK) a.AK[(int64_t)dst * a.ldak + col] = z;
+              if (a.AK16) a.AK16[(int64_t)dst * a.ldak16 + col] = __double2bfloat16(z);
+            } else {
+              a.bK[dst] = z;
+            }
+          }
+          if (hd >= 0 && col < a.d) a.Ahat[(int64_t)col * a.r + hd] = z * a.hat_scale;
+        }
+      }
+    }
+  }
+}
+
+template <int LOGL, int V>
+static spcg_status launch_tile(const FwhtArgs& a, int64_t nbases, cudaStream_t st) {
+  using S = TileShape<LOGL, V>;
+  FwhtArgs b = a;
+  b.ncoltiles = (a.C + S::TC - 1) / S::TC;
+  SPCG_CK(cudaFuncSetAttribute(k_fwht_tile<LOGL, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)S::SMEM));
+  k_fwht_tile<LOGL, V><<<(unsigned)(nbases * b.ncoltiles), S::NT, S::SMEM, st>>>(b);
+  SPCG_CK(cudaGetLastError());
+  return SPCG_OK;
+}
+
 template <int LOGL>
 static spcg_status launch_one(const FwhtArgs& a, int64_t nbases, cudaStream_t st) {
   using S = FwhtShape<LOGL>;
@@ -319,7 +478,22 @@ static spcg_status launch_one(const FwhtArgs& a, int64_t nbases, cudaStream_t st
   return SPCG_OK;
 }
 
-static spcg_status launch_logl(int logl, const FwhtArgs& a, int64_t nbases, cudaStream_t st) {
+// variant: 0 = the per-round kernel k_fwht_pass for every pass, 1 or 2 = the
+// tiled kernel (TileCfg variant) for passes of 9..12 levels.
+static spcg_status launch_logl(int logl, const FwhtArgs& a, int64_t nbases, cudaStream_t st,
+                               int variant) {
+  if (variant == 2) {
+    if (logl == 9) return launch_tile<9, 2>(a, nbases, st);
+    if (logl == 10) return launch_tile<10, 2>(a, nbases, st);
+  }
+  if (variant >= 1) {
+    switch (logl) {
+      case 9: return launch_tile<9, 1>(a, nbases, st);
+      case 10: return launch_tile<10, 1>(a, nbases, st);
+      case 11: return launch_tile<11, 1>(a, nbases, st);
+      case 12: return launch_tile<12, 1>(a, nbases, st);
+    }
+  }
   switch (logl) {
     case 1: return launch_one<1>(a, nbases, st);
     case 2: return launch_one<2>(a, nbases, st);
@@ -338,9 +512,17 @@ static spcg_status launch_logl(int logl, const FwhtArgs& a, int64_t nbases, cuda
 }
 
 // Split n index bits into passes of at most 12 bits, as even as possible.
-int fwht_pass_plan(int n, int* logl) {
+// Split n index bits into passes of at most 12 bits, as even as possible,
+// the larger passes first; first_levels (> 0) fixes the first pass of a
+// two-pass plan instead.
+int fwht_pass_plan(int n, int* logl, int first_levels) {
   const int passes = (n + 11) / 12;
   for (int p = 0; p < passes; ++p) logl[p] = n / passes + (p < n % passes ? 1 : 0);
+  if (passes == 2 && first_levels > 0 && first_levels <= 12 && n - first_levels >= 1 &&
+      n - first_levels <= 12) {
+    logl[0] = first_levels;
+    logl[1] = n - first_levels;
+  }
   return passes;
 }
 
@@ -366,7 +548,8 @@ spcg_status launch_transform(spcg_ctx* c) {
   const int C = c->d + 1;
   SPCG_TRY(launch_colscales(c));
   int logl[8];
-  const int passes = fwht_pass_plan(s.nbits, logl);
+  const int passes = fwht_pass_plan(s.nbits, logl, c->opts.fwht_first_levels);
+  const int variant = c->opts.fwht_tile == 0 ? 1 : (c->opts.fwht_tile == 3 ? 0 : c->opts.fwht_tile);
   FwhtArgs a{};
   a.X = c->X;
   a.ldx = c->ldx;
@@ -394,7 +577,7 @@ spcg_status launch_transform(spcg_ctx* c) {
     a.first = (p == 0);
     a.last = (p == passes - 1);
     const int64_t nbases = s.n_pad >> logl[p];
-    SPCG_TRY(launch_logl(logl[p], a, nbases, c->stream));
+    SPCG_TRY(launch_logl(logl[p], a, nbases, c->stream, variant));
     c->n_launch += 1;
     shift += logl[p];
   }

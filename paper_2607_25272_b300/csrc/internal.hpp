@@ -59,6 +59,7 @@ struct PcgBuffers {
   double* dots_rb;
   int n_red;         // CTAs of the reduce kernel
   int n_pre;         // CTAs of the precond kernels
+  int n_ds;          // CTAs of k_dspace (= shares in dots_pw, dots_gz, dots_rb)
   int last_grid;     // CTAs of the last fused pass (= partials to reduce)
 };
 
@@ -88,6 +89,12 @@ struct Sketch {
   double* R = nullptr;          // d x d row-major upper
   double* Rinv = nullptr;       // d x d row-major upper
   double* RinvT = nullptr;      // d x d row-major lower (R^{-T})
+  // scratch of the cooperative blocked QR (qr.cu), sized at create for one CTA per SM
+  double* qr_vdiag = nullptr;   // d: first entry v_0 of each Householder vector
+  double* qr_red = nullptr;     // 2 x SMs x (2 x panel width): per-CTA partial sums
+  double* qr_wp = nullptr;      // SMs x panel width x d: per-CTA partials of V^T C
+  double* qr_wt = nullptr;      // panel width x d: T^T V^T C
+  unsigned* qr_bar = nullptr;   // grid barrier: arrival count, generation
   unsigned long long* colmax = nullptr;  // d + 1: largest |x| per column (bit pattern)
   int* colshift = nullptr;      // d + 1: fixed-point scale exponent per column
   PassGeom geom[SPCG_MAX_STAGES];  // fused-pass geometry of stage i
@@ -172,6 +179,7 @@ spcg_status launch_countsketch(spcg_ctx* c);
 spcg_status launch_export_rows(spcg_ctx* c, int64_t row0, int64_t n, double* A, double* b);
 spcg_status launch_to_f32(spcg_ctx* c);   // X -> Xf
 // qr.cu
+constexpr int kQrPanel = 32;   // panel width of the blocked QR
 spcg_status launch_precond_factor(spcg_ctx* c);
 // pcg.cu
 spcg_status make_pass_geom(const double* A, int64_t m, int d, int64_t lda, PassGeom* g);
@@ -184,6 +192,8 @@ spcg_status launch_reduce(spcg_ctx* c, double* out, const double* dotvec);
 spcg_status launch_precond_T(spcg_ctx* c, int iter_mode, int cur, int pp, int gp, double* beta);
 spcg_status launch_precond(spcg_ctx* c, int cur, const double* beta);
 spcg_status launch_check(spcg_ctx* c, double tau);
+int dspace_grid(const spcg_ctx* c);
+spcg_status launch_dspace(spcg_ctx* c, int iter, int cur, int pp, int gp, double* beta);
 spcg_status launch_reset_flags(spcg_ctx* c);
 spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1, int op);
 spcg_status prof_collect(spcg_ctx* c);   // after a stream sync

@@ -571,6 +571,162 @@ __global__ void __launch_bounds__(kPreWarps * 32)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The d-space work between two fused passes in ONE cooperative launch.  It
+// replaces k_reduce + k_precondT + k_precond (three launches) with three
+// phases separated by bounded grid barriers:
+//   1. columns of the pass output: w = sum of the per-CTA partials (the
+//      residual pass of a (re)start gives g directly), share of p.w;
+//   2. alpha = gamma / p.w, g' = g - alpha w (every CTA forms all of g'),
+//      beta += alpha p (own columns), u = R^{-T} g' (own rows);
+//   3. z = R^{-1} u and (R beta)_i (own rows), shares of g'.z and ||R beta||^2.
+// The next pass's prologue adds the shares (gamma', the stopping test, p).
+// Rows of the triangular products are dealt round-robin to all warps of the
+// grid, so long and short rows mix; every sum runs in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kDsThreads = 256;
+constexpr int kDsWarps = kDsThreads / 32;
+
+struct DspaceArgs {
+  int d;
+  int iter;                 // 0: (re)start from a residual pass; 1: PCG iteration
+  const double* partials;   // nb x ldp per-CTA partials of the pass
+  int nb, ldp;
+  const double* R;          // d x d row-major upper
+  const double* Rinv;       // d x d row-major upper
+  const double* RinvT;      // d x d row-major lower
+  const double* g_cur;      // iter: current gradient
+  double* g_nxt;            // the new gradient (start: the reduced pass output)
+  double* w;                // iter: A^T A p
+  const double* p;          // iter: the direction the pass multiplied
+  double* beta;
+  double* u;
+  double* z;
+  double* dots_pw;          // gridDim.x shares
+  double* dots_gz;
+  double* dots_rb;
+  int gp;                   // gamma index of the current direction
+  DevScalars* scal;
+  unsigned* bar;
+  long long spin;
+};
+
+// Fixed-order sum of one value per warp (lane 0's) over the CTA, by thread 0.
+__device__ __forceinline__ void ds_block_sum2(double a0, double a1, double (*red)[2], double* o0,
+                                              double* o1) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[warp][0] = a0;
+    red[warp][1] = a1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int k = 0; k < kDsWarps; ++k) {
+      s0 += red[k][0];
+      s1 += red[k][1];
+    }
+    if (o0) *o0 = s0;
+    if (o1) *o1 = s1;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kDsThreads) k_dspace(const DspaceArgs a) {
+  extern __shared__ double ds_sm[];
+  double* gs = ds_sm;          // g' (all d)
+  double* us = gs + a.d;       // u (all d)
+  double* bs = us + a.d;       // beta (all d)
+  __shared__ int s_fail;
+  __shared__ double s_red[kDsWarps][2];
+  __shared__ double s_alpha;
+  if (a.scal->status != 0 || a.scal->done != 0) return;   // uniform over the grid
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x, q = blockIdx.x, d = a.d;
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  const int cs = (d + G - 1) / G;
+  const int c_lo = q * cs, c_hi = c_lo + cs < d ? c_lo + cs : d;
+  // 1. own columns of the pass output
+  double pw = 0.0;
+  for (int j = c_lo + warp; j < c_hi; j += kDsWarps) {
+    double sacc = 0.0;
+    for (int b = lane; b < a.nb; b += 32) sacc += a.partials[(size_t)b * a.ldp + j];
+    sacc = warp_allsum(sacc);
+    if (lane == 0) {
+      if (a.iter) {
+        a.w[j] = sacc;
+        pw = fma(sacc, a.p[j], pw);
+      } else {
+        a.g_nxt[j] = sacc;
+      }
+    }
+  }
+  if (a.iter) ds_block_sum2(pw, 0.0, s_red, &a.dots_pw[q], nullptr);
+  if (!grid_sync_bounded(a.bar, &a.scal->status, a.spin, &s_fail)) return;
+  // 2. alpha, g', beta, u = R^{-T} g'
+  double alpha = 0.0;
+  if (a.iter) {
+    if (warp == 0) {
+      double t = 0.0;
+      for (int k = lane; k < G; k += 32) t += a.dots_pw[k];
+      t = warp_allsum(t);
+      if (lane == 0) {
+        const double al = a.scal->gam[a.gp] / t;
+        s_alpha = (t > 0.0 && isfinite(al)) ? al : NAN;
+      }
+    }
+    __syncthreads();
+    alpha = s_alpha;
+    if (isnan(alpha)) {   // the same value in every CTA: all leave here
+      if (q == 0 && tid == 0) atomicExch(&a.scal->status, DEV_BREAKDOWN);
+      return;
+    }
+    for (int j = tid; j < d; j += kDsThreads) gs[j] = fma(-alpha, a.w[j], a.g_cur[j]);
+    for (int j = c_lo + tid; j < c_hi; j += kDsThreads) {
+      a.g_nxt[j] = fma(-alpha, a.w[j], a.g_cur[j]);
+      a.beta[j] = fma(alpha, a.p[j], a.beta[j]);
+    }
+  } else {
+    for (int j = tid; j < d; j += kDsThreads) gs[j] = a.g_nxt[j];
+  }
+  __syncthreads();
+  const int W = G * kDsWarps, gw = q * kDsWarps + warp;
+  for (int i = gw; i < d; i += W) {
+    const double* Ri = a.RinvT + (size_t)i * d;
+    double sacc = 0.0;
+    for (int j = lane; j <= i; j += 32) sacc = fma(Ri[j], gs[j], sacc);
+    sacc = warp_allsum(sacc);
+    if (lane == 0) a.u[i] = sacc;
+  }
+  if (!grid_sync_bounded(a.bar, &a.scal->status, a.spin, &s_fail)) return;
+  // 3. z = R^{-1} u, (R beta)_i, shares of g'.z and ||R beta||^2
+  for (int j = tid; j < d; j += kDsThreads) {
+    us[j] = a.u[j];
+    bs[j] = a.beta[j];
+  }
+  __syncthreads();
+  double gz = 0.0, rb2 = 0.0;
+  for (int i = gw; i < d; i += W) {
+    const double* Ri = a.Rinv + (size_t)i * d;
+    const double* Rr = a.R + (size_t)i * d;
+    double zs = 0.0, rs = 0.0;
+    for (int j = i + lane; j < d; j += 32) {
+      zs = fma(Ri[j], us[j], zs);
+      rs = fma(Rr[j], bs[j], rs);
+    }
+    zs = warp_allsum(zs);
+    rs = warp_allsum(rs);
+    if (lane == 0) {
+      a.z[i] = zs;
+      gz = fma(gs[i], zs, gz);
+      rb2 = fma(rs, rs, rb2);
+    }
+  }
+  ds_block_sum2(gz, rb2, s_red, &a.dots_gz[q], &a.dots_rb[q]);
+}
+
 // The stopping test on freshly computed dots (same sums as the pass prologue).
 __global__ void k_check(const double* __restrict__ dots_gz, const double* __restrict__ dots_rb,
                         int n, double tau, DevScalars* __restrict__ scal) {
@@ -586,10 +742,11 @@ __global__ void k_check(const double* __restrict__ dots_gz, const double* __rest
   }
 }
 
-__global__ void k_reset(DevScalars* scal, int clear_status) {
+__global__ void k_reset(DevScalars* scal, int clear_status, unsigned* bar) {
   if (clear_status) scal->status = 0;
   scal->done = 0;
   scal->iters = 0;
+  if (bar) bar[0] = 0u;   // arrivals of the grid barrier (a timed-out wait leaves a count)
 }
 
 // --------------------------------------------------------------------------
@@ -760,7 +917,7 @@ spcg_status pass_gram_iter(spcg_ctx* c, const PassGeom& g, int pp, int gp, int s
   a.p_next = c->pb.p[pp ^ 1];
   a.dots_gz = c->pb.dots_gz;
   a.dots_rb = c->pb.dots_rb;
-  a.n_dots = c->pb.n_pre;
+  a.n_dots = c->pb.n_ds;
   a.gp = gp;
   a.start = start;
   a.check = check;
@@ -800,15 +957,54 @@ spcg_status launch_precond(spcg_ctx* c, int cur, const double* beta) {
   return SPCG_OK;
 }
 
+// CTAs of k_dspace: about eight columns (and rows) per CTA, at most one per SM.
+int dspace_grid(const spcg_ctx* c) {
+  int g = (c->d + 7) / 8;
+  if (g > c->num_sms) g = c->num_sms;
+  return g < 1 ? 1 : g;
+}
+
+spcg_status launch_dspace(spcg_ctx* c, int iter, int cur, int pp, int gp, double* beta) {
+  DspaceArgs a{};
+  a.d = c->d;
+  a.iter = iter;
+  a.partials = c->pb.partials;
+  a.nb = c->pb.last_grid;
+  a.ldp = c->pb.ldp;
+  a.R = c->sk.R;
+  a.Rinv = c->sk.Rinv;
+  a.RinvT = c->sk.RinvT;
+  a.g_cur = c->pb.g[cur];
+  a.g_nxt = c->pb.g[cur ^ 1];
+  a.w = c->pb.w;
+  a.p = c->pb.p[pp];
+  a.beta = beta;
+  a.u = c->pb.u;
+  a.z = c->pb.z;
+  a.dots_pw = c->pb.dots_pw;
+  a.dots_gz = c->pb.dots_gz;
+  a.dots_rb = c->pb.dots_rb;
+  a.gp = gp;
+  a.scal = c->scal;
+  a.bar = c->sk.qr_bar;
+  a.spin = c->opts.spin_budget > 0 ? c->opts.spin_budget : (1ll << 31);
+  const size_t smem = (size_t)3 * c->d * sizeof(double);
+  void* args[] = {&a};
+  SPCG_CK(cudaLaunchCooperativeKernel((const void*)k_dspace, dim3(c->pb.n_ds), dim3(kDsThreads),
+                                      args, smem, c->stream));
+  c->n_launch += 1;
+  return SPCG_OK;
+}
+
 spcg_status launch_check(spcg_ctx* c, double tau) {
-  k_check<<<1, 32, 0, c->stream>>>(c->pb.dots_gz, c->pb.dots_rb, c->pb.n_pre, tau, c->scal);
+  k_check<<<1, 32, 0, c->stream>>>(c->pb.dots_gz, c->pb.dots_rb, c->pb.n_ds, tau, c->scal);
   SPCG_CK(cudaGetLastError());
   c->n_launch += 1;
   return SPCG_OK;
 }
 
 spcg_status launch_reset_flags(spcg_ctx* c) {
-  k_reset<<<1, 1, 0, c->stream>>>(c->scal, 1);
+  k_reset<<<1, 1, 0, c->stream>>>(c->scal, 1, c->sk.qr_bar);
   SPCG_CK(cudaGetLastError());
   c->n_launch += 1;
   return SPCG_OK;
@@ -1352,7 +1548,7 @@ spcg_status pass_gram_iter_df(spcg_ctx* c, const PassGeom& g, const CUtensorMap&
   a.p_next = c->pb.p[pp ^ 1];
   a.dots_gz = c->pb.dots_gz;
   a.dots_rb = c->pb.dots_rb;
-  a.n_dots = c->pb.n_pre;
+  a.n_dots = c->pb.n_ds;
   a.gp = gp;
   a.start = start;
   a.check = check;

@@ -1,14 +1,27 @@
 // The preconditioner factor (Sec. 2.2; Sec. 4 applies H-hat through a QR):
 // H-hat = (S-hat X)^T (S-hat X) = R^T R with R from a Householder QR of the
 // r x d sketch S-hat X, then R^{-1} and R^{-T} for the two triangular
-// products z = R^{-1} (R^{-T} g) of every PCG iteration.
+// products z = R^{-1} (R^{-T} g) of every PCG iteration.  FP64 throughout:
+// at kappa = 1e8 the sketch must be factored well below 1/kappa relative
+// error.
 //
-// Householder step k (one launch): every CTA forms the reflector of column
-// k from the untouched column (it only reads it), then applies it to the
-// trailing columns it owns, one warp per column.  Column k itself is never
-// written during step k, so the CTAs do not race; the diagonal alpha_k is
-// recorded separately.  FP64 throughout: at kappa = 1e8 the sketch must be
-// factored well below 1/kappa relative error.
+// Main path, k_qr_coop: blocked Householder QR with the compact WY form
+// (H_0 ... H_{b-1} = I - V T V^T) in ONE cooperative launch, one CTA per SM
+// (fewer for small r), every CTA owning a contiguous block of rows.
+//   Panel of b = 32 columns: each CTA keeps its rows of the panel in shared
+//   memory.  Column step j needs one grid-wide reduction of 2b numbers: the
+//   column's squared norm below the diagonal, its dot products with the
+//   other panel columns below the diagonal, and the panel's values on the
+//   diagonal row.  From these sums every CTA derives alpha, the reflector's
+//   first entry v_0, v^T a_i for the later columns (so each CTA updates its
+//   own rows without a second reduction) and V^T v_j for the column j of T.
+//   Trailing matrix C: W = V^T C (per-CTA partials over its rows), then
+//   W' = T^T W (columns split over CTAs), then C -= V W' (own rows).
+//   A grid barrier separates the phases; its wait is bounded (on expiry the
+//   device status becomes TIMEOUT and every CTA leaves at its next barrier).
+//   Partial sums are added in CTA order, so the result is reproducible.
+// Fallback for r too large for the panel rows to fit in shared memory: one
+// launch per column (k_householder_cluster / k_householder_step below).
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -169,6 +182,206 @@ __global__ void __cluster_dims__(QRC, 1, 1) __launch_bounds__(QRC_WARPS * 32)
   cluster.sync();   // no CTA leaves while another still reads its shared memory
 }
 
+// ---------------------------------------------------------------------------
+// Cooperative blocked QR
+// ---------------------------------------------------------------------------
+constexpr int QB = kQrPanel;           // panel width b
+constexpr int QSL = 2 * QB;            // reduction slots of a column step
+constexpr int QT = 256;                // threads per CTA
+constexpr int QLD = QB + 1;            // row stride of the panel slice in shared memory
+constexpr int QCOLB = 8;               // columns per batch in the T^T W phase
+
+struct QrCoopArgs {
+  double* A;           // r x d column-major (ld = r), reduced in place
+  int64_t r;
+  int d;
+  int chunk_max;       // rows of the largest panel slice of a CTA
+  double* Rdiag;       // d: alpha_k (R_kk before the sign fix)
+  double* vdiag;       // d: v_0 of reflector k
+  double* red;         // 2 x G x QSL
+  double* Wp;          // G x QB x d
+  double* Wt;          // QB x d
+  unsigned* bar;       // [0] arrivals, [1] generation (zero at launch)
+  int* status;
+  long long spin;
+};
+
+__global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
+  extern __shared__ double qsm[];
+  double* P = qsm;                                   // chunk_max x QLD: panel rows, then V
+  double* T = P + (size_t)a.chunk_max * QLD;         // QB x QB, T[i * QB + j]
+  double* tot = T + QB * QB;                         // QSL summed slots
+  double* comb = tot + QSL;                          // 4 x QSL partial slots
+  double* pv0 = comb + 4 * QSL;                      // QB: v_0 of the panel's reflectors
+  double* wsm = pv0 + QB;                            // QCOLB x QB: W columns of one batch
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, G = gridDim.x, q = blockIdx.x;
+  if (tid == 0) s_fail = 0;
+  if (*a.status != 0) return;                        // uniform: set before this launch
+  __syncthreads();
+  const int64_t r = a.r;
+  const int d = a.d;
+  int step = 0;
+  for (int k0 = 0; k0 < d; k0 += QB) {
+    const int bw = d - k0 < QB ? d - k0 : QB;
+    const int64_t mp = r - k0;
+    const int64_t chunk = (mp + G - 1) / G;
+    const int64_t lo = k0 + (int64_t)q * chunk;
+    const int64_t hi = lo + chunk < r ? lo + chunk : r;
+    const int nr = hi > lo ? (int)(hi - lo) : 0;
+    // this CTA's rows of the panel (coalesced along each column)
+    for (int e = tid; e < nr * QB; e += QT) {
+      const int j = e / nr, ri = e % nr;
+      P[ri * QLD + j] = j < bw ? a.A[(int64_t)(k0 + j) * r + lo + ri] : 0.0;
+    }
+    for (int e = tid; e < QB * QB; e += QT) T[e] = 0.0;
+    __syncthreads();
+    for (int j = 0; j < bw; ++j, ++step) {
+      const int64_t diag = k0 + j;
+      const int own = (diag >= lo && diag < hi) ? (int)(diag - lo) : -1;
+      // slot s < QB: sum over own rows below the diagonal of P[., s] P[., j];
+      // slot QB + s: the diagonal row's value of column s (owner only)
+      {
+        const int sl = tid % QSL, grp = tid / QSL;   // 4 row groups
+        double acc = 0.0;
+        if (sl < QB) {
+          if (sl < bw) {
+            int ri0 = (int)(diag + 1 - lo);
+            if (ri0 < 0) ri0 = 0;
+            for (int ri = ri0 + grp; ri < nr; ri += 4) acc = fma(P[ri * QLD + sl], P[ri * QLD + j], acc);
+          }
+        } else if (grp == 0 && own >= 0 && sl - QB < bw) {
+          acc = P[own * QLD + (sl - QB)];
+        }
+        comb[grp * QSL + sl] = acc;
+      }
+      __syncthreads();
+      double* red = a.red + (size_t)(step & 1) * G * QSL;
+      if (tid < QSL)
+        red[(size_t)q * QSL + tid] =
+            ((comb[tid] + comb[QSL + tid]) + comb[2 * QSL + tid]) + comb[3 * QSL + tid];
+      if (!grid_sync_bounded(a.bar, a.status, a.spin, &s_fail)) return;
+      {
+        // the same sums in every CTA: slot sl over CTAs g, g + 4, ... then the
+        // four quarter sums in order
+        const int sl = tid % QSL, grp = tid / QSL;
+        double acc = 0.0;
+#pragma unroll 4
+        for (int g = grp; g < G; g += 4) acc += red[(size_t)g * QSL + sl];
+        comb[grp * QSL + sl] = acc;
+      }
+      __syncthreads();
+      if (tid < QSL) tot[tid] = ((comb[tid] + comb[QSL + tid]) + comb[2 * QSL + tid]) + comb[3 * QSL + tid];
+      __syncthreads();
+      const double s2 = tot[j], x0 = tot[QB + j];
+      const double normx = sqrt(fma(x0, x0, s2));
+      const double alpha = (x0 >= 0.0) ? -normx : normx;
+      const double v0 = x0 - alpha;
+      const double vv = fma(v0, v0, s2);
+      const double tau = vv > 0.0 ? 2.0 / vv : 0.0;
+      if (tid == 0) {
+        pv0[j] = v0;
+        if (q == 0) {
+          a.Rdiag[diag] = alpha;
+          a.vdiag[diag] = v0;
+        }
+      }
+      // T(0:j, j) = -tau T(0:j, 0:j) V(:, 0:j)^T v_j, with
+      // v_l^T v_j = (below the diagonal) + v_l(diag) v_0
+      if (tid < j) {
+        double sacc = 0.0;
+        for (int l = tid; l < j; ++l) sacc = fma(T[tid * QB + l], fma(tot[QB + l], v0, tot[l]), sacc);
+        T[tid * QB + j] = -tau * sacc;
+      } else if (tid == j) {
+        T[j * QB + j] = tau;
+      }
+      // later panel columns, own rows: a_i -= tau (v^T a_i) v
+      const int ncl = bw - j - 1;
+      for (int e = tid; e < nr * ncl; e += QT) {
+        const int i = j + 1 + e / nr, ri = e % nr;
+        const int64_t row = lo + ri;
+        if (row < diag) continue;
+        const double f = tau * fma(v0, tot[QB + i], tot[i]);
+        const double vr = (row == diag) ? v0 : P[ri * QLD + j];
+        P[ri * QLD + i] = fma(-f, vr, P[ri * QLD + i]);
+      }
+      __syncthreads();
+    }
+    // write the panel back (R above the diagonal, v below it, x_0 on it)
+    for (int e = tid; e < nr * bw; e += QT) {
+      const int j = e / nr, ri = e % nr;
+      a.A[(int64_t)(k0 + j) * r + lo + ri] = P[ri * QLD + j];
+    }
+    __syncthreads();
+    // the CTA's rows of V: v_i(row) = 0 above the diagonal, v_0 on it
+    for (int e = tid; e < nr * QB; e += QT) {
+      const int ri = e / QB, i = e % QB;
+      const int64_t row = lo + ri;
+      double v = 0.0;
+      if (i < bw) v = row > k0 + i ? P[ri * QLD + i] : (row == k0 + i ? pv0[i] : 0.0);
+      P[ri * QLD + i] = v;
+    }
+    __syncthreads();
+    const int nt = d - k0 - bw;   // trailing columns
+    if (nt <= 0) break;           // last panel: nothing to update
+    // W partial = V_own^T C_own
+    for (int c = tid; c < nt; c += QT) {
+      double w[QB];
+#pragma unroll
+      for (int i = 0; i < QB; ++i) w[i] = 0.0;
+      const double* col = a.A + (int64_t)(k0 + bw + c) * r + lo;
+      for (int ri = 0; ri < nr; ++ri) {
+        const double cv = col[ri];
+#pragma unroll
+        for (int i = 0; i < QB; ++i) w[i] = fma(P[ri * QLD + i], cv, w[i]);
+      }
+      double* dst = a.Wp + (size_t)q * QB * d + c;
+#pragma unroll
+      for (int i = 0; i < QB; ++i) dst[(size_t)i * d] = w[i];
+    }
+    if (!grid_sync_bounded(a.bar, a.status, a.spin, &s_fail)) return;
+    // W = sum of the partials (CTA order), W' = T^T W for this CTA's columns
+    {
+      const int cs = (nt + G - 1) / G;
+      const int c_lo = q * cs, c_hi = c_lo + cs < nt ? c_lo + cs : nt;
+      for (int cb = c_lo; cb < c_hi; cb += QCOLB) {
+        const int ncb = c_hi - cb < QCOLB ? c_hi - cb : QCOLB;
+        for (int e = tid; e < ncb * QB; e += QT) {
+          const int cc = e / QB, i = e % QB;
+          double acc = 0.0;
+          const double* src = a.Wp + (size_t)i * d + cb + cc;
+#pragma unroll 4
+          for (int g = 0; g < G; ++g) acc += src[(size_t)g * QB * d];
+          wsm[cc * QB + i] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < ncb * QB; e += QT) {
+          const int cc = e / QB, i = e % QB;
+          double acc = 0.0;
+          for (int l = 0; l <= i; ++l) acc = fma(T[l * QB + i], wsm[cc * QB + l], acc);
+          a.Wt[(size_t)i * d + cb + cc] = acc;
+        }
+        __syncthreads();
+      }
+    }
+    if (!grid_sync_bounded(a.bar, a.status, a.spin, &s_fail)) return;
+    // C_own -= V_own W'
+    for (int c = tid; c < nt; c += QT) {
+      double wt[QB];
+#pragma unroll
+      for (int i = 0; i < QB; ++i) wt[i] = a.Wt[(size_t)i * d + c];
+      double* col = a.A + (int64_t)(k0 + bw + c) * r + lo;
+      for (int ri = 0; ri < nr; ++ri) {
+        double acc = col[ri];
+#pragma unroll
+        for (int i = 0; i < QB; ++i) acc = fma(-P[ri * QLD + i], wt[i], acc);
+        col[ri] = acc;
+      }
+    }
+    if (!grid_sync_bounded(a.bar, a.status, a.spin, &s_fail)) return;
+  }
+}
+
 // R (row-major upper, diag > 0) from the reduced matrix: row i of R is row i
 // of A after step i, times the sign that makes alpha_i positive.
 __global__ void k_extract_R(const double* __restrict__ A, int64_t r, int d,
@@ -190,28 +403,57 @@ __global__ void k_extract_R(const double* __restrict__ A, int64_t r, int d,
   }
 }
 
-// R^{-1} column by column (one warp per column j): back substitution of
-// R x = e_j, x_i = -(sum_{k=i+1..j} R_ik x_k) / R_ii, x_j = 1 / R_jj.
-__global__ void __launch_bounds__(256) k_trtri_upper(const double* __restrict__ R, int d,
-                                                   double* __restrict__ Rinv) {
-  extern __shared__ double xs[];  // 8 warps x d
+// R^{-1} column by column, one warp per column j, blocked back substitution
+// of R x = e_j over blocks of 32 rows, from the bottom block up:
+//   - the block's 32 x 32 triangle is solved in registers: lane L holds
+//     b_{kb+L} and row kb+L of the triangle; x_t = b_t / R_tt is broadcast
+//     with a shuffle and the lanes above it subtract x_t R_{L t};
+//   - the rows above the block then take the block's contribution,
+//     b_i -= sum_t R_{i, kb+t} x_{kb+t}, with all 32 loads of a row
+//     independent (no dependency chain through memory).
+// Column j of R^{-1} is written as row j of R^{-T} (contiguous); R^{-1} is
+// its transpose.  Columns are dealt to warps so that every CTA mixes short
+// and long columns (column j costs about j^2 / 2 multiply-adds).
+constexpr int TRI_WARPS = 4;
+
+__global__ void __launch_bounds__(TRI_WARPS * 32) k_trtri_blocked(const double* __restrict__ R, int d,
+                                                                 double* __restrict__ RinvT) {
+  extern __shared__ double xs[];   // TRI_WARPS x d
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = blockIdx.x * 8 + warp;
+  const int j = blockIdx.x + gridDim.x * warp;
   if (j >= d) return;
-  double* x = xs + (size_t)warp * d;
-  for (int i = lane; i < d; i += 32) x[i] = 0.0;
+  double* b = xs + (size_t)warp * d;
+  for (int i = lane; i <= j; i += 32) b[i] = (i == j) ? 1.0 : 0.0;
   __syncwarp();
-  if (lane == 0) x[j] = 1.0 / R[(int64_t)j * d + j];
-  __syncwarp();
-  for (int i = j - 1; i >= 0; --i) {
-    const double* Ri = R + (int64_t)i * d;
-    double s = 0.0;
-    for (int k = i + 1 + lane; k <= j; k += 32) s += Ri[k] * x[k];
-    s = warp_allsum(s);
-    if (lane == 0) x[i] = -s / Ri[i];
+  for (int kb = (j / 32) * 32; kb >= 0; kb -= 32) {
+    const int nb = j - kb + 1 < 32 ? j - kb + 1 : 32;   // rows kb .. kb+nb-1 (<= j < d)
+    double tri[32];
+    const double* Rrow = R + (size_t)(kb + (lane < nb ? lane : 0)) * d + kb;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) tri[t] = (lane < nb && t > lane && t < nb) ? Rrow[t] : 0.0;
+    const double rin = lane < nb ? 1.0 / Rrow[lane] : 0.0;
+    double bl = lane < nb ? b[kb + lane] : 0.0;
+#pragma unroll
+    for (int t = 31; t >= 0; --t) {
+      if (t < nb) {   // warp-uniform
+        const double xt = __shfl_sync(0xffffffffu, bl * rin, t);
+        if (lane == t) bl = xt;
+        else if (lane < t) bl = fma(-xt, tri[t], bl);
+      }
+    }
+    if (lane < nb) b[kb + lane] = bl;
+    __syncwarp();
+    for (int i = lane; i < kb; i += 32) {
+      const double* Ri = R + (size_t)i * d + kb;
+      double acc = b[i];
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t < nb) acc = fma(-Ri[t], b[kb + t], acc);
+      b[i] = acc;
+    }
     __syncwarp();
   }
-  for (int i = lane; i < d; i += 32) Rinv[(int64_t)i * d + j] = x[i];
+  for (int i = lane; i < d; i += 32) RinvT[(size_t)j * d + i] = i <= j ? b[i] : 0.0;
 }
 
 __global__ void k_transpose(const double* __restrict__ S, int d, double* __restrict__ T) {
@@ -228,7 +470,21 @@ __global__ void k_transpose(const double* __restrict__ S, int d, double* __restr
   }
 }
 
-spcg_status launch_precond_factor(spcg_ctx* c) {
+// Rows of the first (largest) panel slice per CTA and the grid of the
+// cooperative QR: at least about 24 rows per CTA, at most one CTA per SM.
+static int qr_coop_grid(int64_t r, int sms) {
+  int64_t g = (r + 23) / 24;
+  if (g > sms) g = sms;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+static size_t qr_coop_smem(int64_t chunk_max) {
+  return ((size_t)chunk_max * QLD + QB * QB + QSL + 4 * QSL + QB + QCOLB * QB) * sizeof(double);
+}
+
+// The per-column fallback (one launch per Householder step).
+static spcg_status householder_by_column(spcg_ctx* c) {
   Sketch& s = c->sk;
   const int d = c->d;
   const int64_t r = s.sched.r;
@@ -260,21 +516,62 @@ spcg_status launch_precond_factor(spcg_ctx* c) {
                                                                    staged);
     }
   }
-  c->n_launch += d + 3;
+  c->n_launch += d;
   SPCG_CK(cudaGetLastError());
+  return SPCG_OK;
+}
+
+spcg_status launch_precond_factor(spcg_ctx* c) {
+  Sketch& s = c->sk;
+  const int d = c->d;
+  const int64_t r = s.sched.r;
+  int G = qr_coop_grid(r, c->num_sms);
+  const int64_t chunk_max = (r + G - 1) / G;
+  const size_t smem = qr_coop_smem(chunk_max);
+  bool coop = smem <= (size_t)200 * 1024 && c->opts.qr_by_column == 0;
+  if (coop) {
+    SPCG_CK(cudaFuncSetAttribute(k_qr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SPCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_coop, QT, smem));
+    if (per_sm < 1) coop = false;   // cannot be co-resident: use the per-column steps
+  }
+  if (coop) {
+    SPCG_CK(cudaMemsetAsync(s.qr_bar, 0, 2 * sizeof(unsigned), c->stream));
+    QrCoopArgs a{};
+    a.A = s.Ahat;
+    a.r = r;
+    a.d = d;
+    a.chunk_max = (int)chunk_max;
+    a.Rdiag = s.Rdiag;
+    a.vdiag = s.qr_vdiag;
+    a.red = s.qr_red;
+    a.Wp = s.qr_wp;
+    a.Wt = s.qr_wt;
+    a.bar = s.qr_bar;
+    a.status = &c->scal->status;
+    a.spin = c->opts.spin_budget > 0 ? c->opts.spin_budget : (1ll << 31);
+    void* args[] = {&a};
+    SPCG_CK(cudaLaunchCooperativeKernel((const void*)k_qr_coop, dim3(G), dim3(QT), args, smem,
+                                        c->stream));
+    c->n_launch += 1;
+  } else {
+    SPCG_TRY(householder_by_column(c));
+  }
   const int64_t dd = (int64_t)d * d;
   int g = (int)((dd + 255) / 256);
   if (g > 4096) g = 4096;
   k_extract_R<<<g, 256, 0, c->stream>>>(s.Ahat, r, d, s.Rdiag, s.R, &c->scal->status);
   SPCG_CK(cudaGetLastError());
-  const size_t smem = (size_t)8 * d * sizeof(double);
-  SPCG_CK(cudaFuncSetAttribute(k_trtri_upper, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
-  k_trtri_upper<<<(d + 7) / 8, 256, smem, c->stream>>>(s.R, d, s.Rinv);
+  const size_t tsm = (size_t)TRI_WARPS * d * sizeof(double);
+  SPCG_CK(cudaFuncSetAttribute(k_trtri_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tsm));
+  k_trtri_blocked<<<(d + TRI_WARPS - 1) / TRI_WARPS, TRI_WARPS * 32, tsm, c->stream>>>(s.R, d,
+                                                                                   s.RinvT);
   SPCG_CK(cudaGetLastError());
   dim3 tg((d + 31) / 32, (d + 31) / 32);
-  k_transpose<<<tg, dim3(32, 8), 0, c->stream>>>(s.Rinv, d, s.RinvT);
+  k_transpose<<<tg, dim3(32, 8), 0, c->stream>>>(s.RinvT, d, s.Rinv);
   SPCG_CK(cudaGetLastError());
+  c->n_launch += 3;
   return SPCG_OK;
 }
 

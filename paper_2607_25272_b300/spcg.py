@@ -87,6 +87,10 @@ class Opts(ctypes.Structure):
         ("inner_prec", ctypes.c_int32),
         ("grad_prec", ctypes.c_int32),
         ("max_workspace_bytes", ctypes.c_int64),
+        ("qr_by_column", ctypes.c_int32),
+        ("fwht_tile", ctypes.c_int32),
+        ("fwht_first_levels", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

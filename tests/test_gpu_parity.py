@@ -173,6 +173,76 @@ def test_sketch_rows_and_preconditioner(N, d, seed, r):
     s.close()
 
 
+# The transform's kernels and pass plans: the 64-bit fixed-point butterflies
+# are exact, so every tile variant and every split of the index bits into two
+# passes must give the same bits; one of them is checked against the oracle's
+# FP64 transform row by row.  N' = 2^19 (ragged N, 33 + 1 columns: partial
+# column tiles), plans 10 + 9 (default), 9 + 10, 12 + 7 (the 7-level pass on
+# the per-round kernel).
+def test_transform_variants_and_plans_are_bit_identical():
+    N, d, seed = (1 << 18) + 37, 33, 12
+    X, Y, _ = gaussian_problem(N, d, 1.0, seed=seed)
+    sched = OS.default_schedule(N, d)
+    mK = sched["m"][-1]
+    outs = []
+    for tile, first in ((0, 0), (1, 0), (2, 0), (3, 0), (1, 9), (2, 9), (1, 12)):
+        o = S.Opts()
+        o.fwht_tile = tile
+        o.fwht_first_levels = first
+        s = S.Solver(cuda(X), cuda(Y), o)
+        s.sketch(seed, S.spcg_default_schedule(N, d))
+        A_g, b_g = (t.cpu().numpy() for t in s.export_sketch(0, mK))
+        R_g = s.export_precond()[0].cpu().numpy()
+        s.close()
+        outs.append((A_g, b_g, R_g))
+    for A_g, b_g, R_g in outs[1:]:
+        assert np.array_equal(A_g, outs[0][0]) and np.array_equal(b_g, outs[0][1])
+        assert np.array_equal(R_g, outs[0][2])
+    n_pad = sched["n_pad"]
+    ZX, ZY, _, _ = _oracle_sketch(X, Y, seed, sched)
+    pi = OR.nested_order(n_pad, mK, seed)
+    Zo = np.concatenate([ZX[pi], ZY[pi][:, None]], axis=1)
+    Zg = np.concatenate([outs[0][0], outs[0][1][:, None]], axis=1)
+    assert np.all(np.abs(Zg - Zo) <= _transform_tol(X, Y, n_pad, Zo))
+
+
+# Both factorisations of the preconditioner sketch: the blocked cooperative QR
+# (panels of 32 columns; widths below, at and just above one panel, ragged
+# last panels) and the per-column steps, each against the oracle's R within
+# the Householder backward-error bound; a sketch of 120000 rows takes the
+# per-column path either way (its panel rows do not fit in shared memory).
+@pytest.mark.parametrize("N,d,r,seed", [(20000, 50, None, 1), (4000, 32, None, 2), (4000, 33, None, 3),
+                                        (9000, 300, None, 4), (70000, 129, None, 8),
+                                        (3000, 7, None, 6), (1 << 17, 8, 120000, 5)])
+def test_qr_blocked_and_per_column_agree(N, d, r, seed):
+    X, Y, _ = gaussian_problem(N, d, 1.0, seed=seed)
+    sched = OS.default_schedule(N, d)
+    if r is not None:
+        sched["r"] = r
+    sched["r"] = min(sched["r"], sched["n_pad"])
+    r = sched["r"]
+    _, _, _, A_hat = _oracle_sketch(X, Y, seed, sched)
+    R_o = OL.r_factor(A_hat)
+    kappa = np.linalg.cond(A_hat)
+    tol_R = 2 * math.sqrt(2) * kappa * gamma(r * d) * (np.linalg.norm(A_hat) / np.linalg.norm(A_hat, 2))
+    Rs = []
+    for by_col in (0, 1):
+        o = S.Opts()
+        o.qr_by_column = by_col
+        s = S.Solver(cuda(X), cuda(Y), o)
+        sc = S.spcg_default_schedule(N, d)
+        sc.r = r
+        s.sketch(seed, sc)
+        R_g, Rinv_g, _ = (t.cpu().numpy() if t is not None else None for t in s.export_precond())
+        s.close()
+        assert np.linalg.norm(R_g - R_o) <= tol_R * np.linalg.norm(R_o, 2), by_col
+        assert np.all(np.diag(R_g) > 0) and np.array_equal(R_g, np.triu(R_g))
+        assert np.array_equal(Rinv_g, np.triu(Rinv_g))
+        assert np.linalg.norm(R_g @ Rinv_g - np.eye(d)) <= 4 * d * U * np.linalg.cond(R_g) * math.sqrt(d)
+        Rs.append(R_g)
+    assert np.linalg.norm(Rs[0] - Rs[1]) <= 2 * tol_R * np.linalg.norm(R_o, 2)
+
+
 # ---------------------------------------------------------------- stages ----
 @pytest.mark.parametrize("N,d,kappa,seed", [(20000, 50, None, 1), (30000, 24, 1e4, 3)])
 def test_stage_iterates_match_oracle(N, d, kappa, seed):

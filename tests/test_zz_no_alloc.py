@@ -12,6 +12,8 @@ second call reuses the array left by the first).
 This file is collected last so that a failure here does not hide the other
 GPU tests in a run that stops at the first failure.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -46,6 +48,7 @@ def test_noalloc_pass_matches_context_pass_twice(m, d):
     bound = 2 * gamma(m + d) * (np.abs(A).T @ (np.abs(A) @ np.abs(p)))
     for call in range(2):
         w = torch.full((d,), np.nan, dtype=torch.float64, device="cuda")
+        gc.collect()                      # no unrelated frees inside the measured call
         torch.cuda.synchronize()
         free0, _ = torch.cuda.mem_get_info()
         alloc0 = torch.cuda.memory_allocated()
@@ -54,8 +57,8 @@ def test_noalloc_pass_matches_context_pass_twice(m, d):
         if call == 1:
             # the property the entry point exists for: the second call (the
             # first may load the kernels' module) takes no device memory
-            assert torch.cuda.mem_get_info()[0] == free0
-            assert torch.cuda.memory_allocated() == alloc0
+            assert torch.cuda.mem_get_info()[0] >= free0
+            assert torch.cuda.memory_allocated() <= alloc0
         w = w.cpu().numpy()
         assert np.all(np.abs(w - w_ctx) <= bound)
         assert np.all(np.abs(w - A.T @ (A @ p)) <= bound)
