@@ -55,10 +55,10 @@ WORKLOADS = {
 WARM_SAMPLE_ROWS = 1 << 14    # oracle warm-up sample of the reference arm
 NOMINAL_FP64_TFLOPS = 1.25    # B300 FP64, nominal (context only)
 # DRAM bytes per algorithmic byte of k_pass (FP64), from the ncu capture of
-# this kernel on a 262144 x 500 operand: read 1.048699 GB + wrote 3.254784 MB
-# for 1.048576 GB of rows.  Set to None whenever the kernel changes after the
-# capture.
-K_PASS_TRAFFIC_RATIO = (1.048699e9 + 3.254784e6) / 1.048576e9
+# this kernel on a 262144 x 500 operand: read 1.048634624 GB + wrote
+# 2.704384 MB for 1.048576 GB of rows.  Set to None whenever the kernel changes
+# after the capture.
+K_PASS_TRAFFIC_RATIO = (1.048634624e9 + 2.704384e6) / 1.048576e9
 
 
 def make_problem(w, N=None, seed_offset=0):
@@ -649,6 +649,63 @@ def run_sketch_only(args, w, local_rank):
     s.close()
 
 
+def run_solve_only(args, w, local_rank):
+    """spcg_solve alone on a rows x d Gaussian problem drawn on the GPU (for
+    profiling the solve's kernels at a chosen size)."""
+    import torch
+
+    from paper_2607_25272_b300 import spcg as S
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1)
+    m, d = args.rows, w["d"]
+    X = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g)
+    Y = torch.randn(m, dtype=torch.float64, device=dev, generator=g)
+    s = S.Solver(X, Y)
+    stream = torch.cuda.current_stream(dev)
+    ms, outs = time_solves(s, 1, None, args.steps, args.warmup, stream)
+    _, info, st = outs[-1]
+    print(json.dumps({"kernel": "spcg_solve", "rows": m, "d": d, "ms_per_call": ms,
+                      "status": S.STATUS[st], "launches": info.launches,
+                      "refine_iters": info.refine_iters}), flush=True)
+    s.close()
+
+
+def run_batched_only(args, w, local_rank):
+    """The batched persistent kernel alone on a batch of args.batch problems of
+    the batched workload's recipe, drawn on the GPU (default chunk sizes)."""
+    import torch
+
+    from paper_2607_25272_b300 import spcg as S
+    from paper_2607_25272_b300.inputs import scaled_columns_problem_device
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    rng = np.random.default_rng(w["seed"])
+    Xs, Ys = [], []
+    for i in range(args.batch):
+        N = int(rng.integers(1 << 12, (1 << 17) + 1))
+        d = int(rng.integers(16, 257))
+        X, Y, _ = scaled_columns_problem_device(N, d, 1e-3, 1e3, w["sigma"],
+                                                seed=w["seed"] * 100000 + i, device=dev,
+                                                dtype=torch.float32)
+        ld = (d + 3) // 4 * 4
+        Xp = torch.zeros((N, ld), dtype=torch.float32, device=dev)
+        Xp[:, :d] = X
+        Xs.append(Xp[:, :d])
+        Ys.append(Y)
+    B = S.Batch(Xs, Ys)
+    for _ in range(args.warmup):
+        B.solve(w["seed"], w["tol"])
+    times = [B.solve(w["seed"], w["tol"])[3] for _ in range(args.steps)]
+    rc, st, it, _ = B.solve(w["seed"], w["tol"])
+    nbytes = sum(X.shape[0] * X.shape[1] * 4 for X in Xs)
+    print(json.dumps({"kernel": "k_batched_spcg", "problems": args.batch,
+                      "ms_per_call": float(np.median(times)), "status_ok": sum(v == 0 for v in st),
+                      "x_bytes_fp32": nbytes, "stage2_iters_sum": int(sum(it))}), flush=True)
+    B.close()
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
 
@@ -845,9 +902,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the nested c3/c4/c5 comparisons of the default run")
-    ap.add_argument("--kernel", default=None, choices=[None, "pass", "sketch"],
+    ap.add_argument("--kernel", default=None, choices=[None, "pass", "sketch", "solve", "batched"],
                     help="time one kernel alone instead of the solve")
     ap.add_argument("--rows", type=int, default=1 << 18)
+    ap.add_argument("--batch", type=int, default=32, help="problems for --kernel batched")
     ap.add_argument("--weights", default=None, help="schedule model weights (npz) for c5")
     ap.add_argument("--ncu-region", default=None, choices=[None, "plain", "mixed"],
                     help="bracket the timed solves of this form with cudaProfilerStart/Stop "
@@ -872,6 +930,10 @@ def main():
         run_pass_only(args, w, local_rank)
     elif args.kernel == "sketch":
         run_sketch_only(args, w, local_rank)
+    elif args.kernel == "solve":
+        run_solve_only(args, w, local_rank)
+    elif args.kernel == "batched":
+        run_batched_only(args, w, local_rank)
     elif args.impl == "ours" and args.workload == "c3":
         print_nested(args, w, run_forms(args, w), "bf16/f32/f64")
     elif args.impl == "ours" and args.workload == "c4":

@@ -130,9 +130,10 @@ typedef struct {
                                blocked cooperative QR (same factorisation,
                                slower; for comparison)                         */
   int32_t fwht_tile;        /* transform passes of 9..12 levels: 0 = default
-                               (1), 1 = 128 KB tiles, one CTA per SM, 2 = 64 KB
-                               tiles, two CTAs per SM (9 or 10 levels; others
-                               as 1), 3 = the per-round pass kernel           */
+                               (the per-round pass kernel, as 3), 1 = 128 KB
+                               tiles, one CTA per SM, 2 = 64 KB tiles, two CTAs
+                               per SM (9 or 10 levels; others as 1), 3 = the
+                               per-round pass kernel; all give the same bits  */
   int32_t fwht_first_levels; /* levels of the first of two transform passes;
                                0 = split evenly                               */
   int32_t reserved;         /* set to 0                                         */
@@ -291,14 +292,22 @@ spcg_status spcg_solve(spcg_ctx* ctx, uint64_t seed, const spcg_schedule* sched,
  *   stream cudaStream_t for the copies and the solve (NULL = default stream)
  *   beta   host, d FP64 output (the last iterate when SPCG_E_NOT_CONVERGED)
  *   info   host, may be NULL
- * Allocates device copies of X (N x d, rows padded to an even count), Y and
- * beta plus a context, and frees all of it before returning; synchronises
- * `stream`.  Errors: SPCG_E_INVALID_ARG, SPCG_E_OOM, SPCG_E_CUDA and those of
- * spcg_solve.
+ * The device copies of X (N x d, rows padded to an even count), Y and beta
+ * and the context's workspace come from a stream-ordered memory pool that the
+ * library keeps per device: freed at the end of the call, the memory stays in
+ * the pool for the next call (of any size) instead of going back to the
+ * device, so repeated calls skip the allocation cost.  spcg_host_pool_trim
+ * hands it back.  Synchronises `stream`.  Errors: SPCG_E_INVALID_ARG,
+ * SPCG_E_OOM, SPCG_E_CUDA and those of spcg_solve.
  */
 spcg_status spcg_solve_host(const double* X, const double* Y, int64_t N, int32_t d, int64_t ldx,
                             uint64_t seed, const spcg_schedule* sched, const spcg_opts* opts,
                             void* stream, double* beta, spcg_info* info);
+
+/* Return the memory kept by spcg_solve_host's pools to the devices (every
+ * device that has one).  Call when no spcg_solve_host is running.  Errors:
+ * SPCG_E_CUDA. */
+spcg_status spcg_host_pool_trim(void);
 
 /* ----- Lower-level entry points (same kernels; for parity checks) ----- */
 

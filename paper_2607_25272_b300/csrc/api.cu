@@ -3,6 +3,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -25,7 +27,8 @@ static spcg_status dalloc(spcg_ctx* c, T** p, size_t count) {
   if (c->opts.max_workspace_bytes > 0 &&
       c->ws_bytes + bytes > (size_t)c->opts.max_workspace_bytes)
     return SPCG_E_OOM;
-  SPCG_CK(cudaMalloc((void**)p, bytes));
+  if (c->pool) SPCG_CK(cudaMallocFromPoolAsync((void**)p, bytes, c->pool, c->stream));
+  else SPCG_CK(cudaMalloc((void**)p, bytes));
   c->ws_sizes[(const void*)*p] = bytes;
   c->ws_bytes += bytes;
   return SPCG_OK;
@@ -39,7 +42,8 @@ static void dfree(spcg_ctx* c, T*& p) {
       c->ws_bytes -= it->second;
       c->ws_sizes.erase(it);
     }
-    cudaFree((void*)p);
+    if (c->pool) cudaFreeAsync((void*)p, c->stream);
+    else cudaFree((void*)p);
   }
   p = nullptr;
 }
@@ -53,7 +57,7 @@ static spcg_status qr_alloc(spcg_ctx* c) {
   SPCG_TRY(dalloc(c, &s.qr_red, (size_t)2 * G * 2 * kQrPanel));
   SPCG_TRY(dalloc(c, &s.qr_wp, (size_t)G * kQrPanel * d));
   SPCG_TRY(dalloc(c, &s.qr_wt, (size_t)kQrPanel * d));
-  SPCG_TRY(dalloc(c, &s.qr_bar, (size_t)2));
+  SPCG_TRY(dalloc(c, &s.qr_bar, (size_t)kBarWords));
   return SPCG_OK;
 }
 
@@ -363,14 +367,49 @@ extern "C" spcg_status spcg_tuned_schedule(int64_t N, int32_t d, spcg_schedule* 
   return SPCG_OK;
 }
 
-extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, int32_t d,
-                                   int64_t ldx, void* stream, const spcg_opts* opts,
-                                   spcg_ctx** out) {
+// The stream-ordered memory pool of spcg_solve_host, one per device, created
+// on first use with a release threshold of "never": memory freed at the end
+// of a call stays in the pool for the next call (spcg_host_pool_trim
+// returns it to the device).
+namespace {
+struct HostPool {
+  std::mutex mu;
+  cudaMemPool_t pool = nullptr;
+};
+HostPool g_host_pools[64];
+
+spcg_status host_pool(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= 64) return SPCG_E_INVALID_ARG;
+  HostPool& hp = g_host_pools[dev];
+  std::lock_guard<std::mutex> lock(hp.mu);
+  if (!hp.pool) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    SPCG_CK(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = ~0ull;
+    if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return from_cuda(cudaGetLastError());
+    }
+    hp.pool = p;
+  }
+  *out = hp.pool;
+  return SPCG_OK;
+}
+}  // namespace
+
+static spcg_status create_impl(const double* X, const double* Y, int64_t N, int32_t d,
+                               int64_t ldx, void* stream, const spcg_opts* opts,
+                               cudaMemPool_t pool, spcg_ctx** out) {
   if (!out) return SPCG_E_INVALID_ARG;
   *out = nullptr;
   if (!X || !Y || d < 1 || d > SPCG_MAX_D || N <= d || N > (int64_t(1) << 30) || ldx < d)
     return SPCG_E_INVALID_ARG;
   spcg_ctx* c = new spcg_ctx();
+  c->pool = pool;
   c->stream = (cudaStream_t)stream;
   if (opts) c->opts = *opts;
   c->N = N;
@@ -452,6 +491,12 @@ extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, 
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(SPCG_E_CUDA);
   *out = c;
   return SPCG_OK;
+}
+
+extern "C" spcg_status spcg_create(const double* X, const double* Y, int64_t N, int32_t d,
+                                   int64_t ldx, void* stream, const spcg_opts* opts,
+                                   spcg_ctx** out) {
+  return create_impl(X, Y, N, d, ldx, stream, opts, nullptr, out);
 }
 
 extern "C" void spcg_destroy(spcg_ctx* c) {
@@ -664,20 +709,28 @@ extern "C" spcg_status spcg_solve_host(const double* X, const double* Y, int64_t
       ldx < d)
     return SPCG_E_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  SPCG_CK(cudaGetDevice(&dev));
+  cudaMemPool_t pool = nullptr;
+  SPCG_TRY(host_pool(dev, &pool));
   const int64_t ld = (d + 1) & ~int64_t(1);   // device rows 16-byte aligned (TMA stride rule)
   double *Xd = nullptr, *Yd = nullptr, *bd = nullptr;
   spcg_ctx* c = nullptr;
   spcg_status res = SPCG_OK;
-  cudaError_t e = cudaMalloc((void**)&Xd, (size_t)N * ld * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&Yd, (size_t)N * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&bd, (size_t)d * sizeof(double));
-  if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(Xd, ld * sizeof(double), X, ldx * sizeof(double), d * sizeof(double), N,
-                          cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMallocFromPoolAsync((void**)&Xd, (size_t)N * ld * sizeof(double), pool, st);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&Yd, (size_t)N * sizeof(double), pool, st);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&bd, (size_t)d * sizeof(double), pool, st);
+  if (e == cudaSuccess) {
+    if (ldx == ld)
+      e = cudaMemcpyAsync(Xd, X, (size_t)N * ld * sizeof(double), cudaMemcpyHostToDevice, st);
+    else
+      e = cudaMemcpy2DAsync(Xd, ld * sizeof(double), X, ldx * sizeof(double), d * sizeof(double),
+                            N, cudaMemcpyHostToDevice, st);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(Yd, Y, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) res = from_cuda(e);
-  if (res == SPCG_OK) res = spcg_create(Xd, Yd, N, d, ld, stream, opts, &c);
+  if (res == SPCG_OK) res = create_impl(Xd, Yd, N, d, ld, stream, opts, pool, &c);
   spcg_status solve_st = SPCG_OK;
   if (res == SPCG_OK) {
     solve_st = spcg_solve(c, seed, sched, bd, info);
@@ -688,12 +741,21 @@ extern "C" spcg_status spcg_solve_host(const double* X, const double* Y, int64_t
       if (e != cudaSuccess) res = from_cuda(e);
     }
   }
-  if (c) spcg_destroy(c);
-  if (!c && res != SPCG_OK) cudaStreamSynchronize(st);   // copies may still read X, Y
-  cudaFree(Xd);
-  cudaFree(Yd);
-  cudaFree(bd);
+  if (c) spcg_destroy(c);   // synchronises the stream, then returns its workspace to the pool
+  if (Xd) cudaFreeAsync(Xd, st);
+  if (Yd) cudaFreeAsync(Yd, st);
+  if (bd) cudaFreeAsync(bd, st);
+  cudaStreamSynchronize(st);
   return res != SPCG_OK ? res : solve_st;
+}
+
+extern "C" spcg_status spcg_host_pool_trim(void) {
+  for (int dev = 0; dev < 64; ++dev) {
+    HostPool& hp = g_host_pools[dev];
+    std::lock_guard<std::mutex> lock(hp.mu);
+    if (hp.pool) SPCG_CK(cudaMemPoolTrimTo(hp.pool, 0));
+  }
+  return SPCG_OK;
 }
 
 extern "C" spcg_status spcg_export_sketch(spcg_ctx* c, int64_t row0, int64_t nrows, double* A,

@@ -157,11 +157,21 @@ struct BShared {
 // b FP64 (stage start, FP32 arithmetic);  mode 2: true gradient in
 // double-FP32.  The result lands in sh.red (per warp) and is summed into
 // out (FP64) in warp order.
-__device__ bool stream_pass(BShared& sh, unsigned char* ring, size_t ring_bytes, const float* A,
-                            int64_t m, int64_t ld, int d, int tile_rows, int mode,
-                            const double* bvec64, const float* bvec32, double* out,
-                            long long spin) {
+//
+// A row is handled by LW lanes (LW = 32 / rows per warp, the smallest power
+// of two with 8 LW >= d): lane s of a group owns columns s, s + LW, ...,
+// s + 7 LW, so narrow problems put several rows in one warp instead of
+// leaving most lanes idle.  Row dot products reduce over the LW lanes of a
+// group (xor shuffles below LW); at the end the groups' column sums are
+// added across the warp (xor shuffles at LW and above) in a fixed order.
+template <int LW>
+__device__ bool stream_pass_lw(BShared& sh, unsigned char* ring, size_t ring_bytes,
+                               const float* A, int64_t m, int64_t ld, int d, int tile_rows,
+                               int mode, const double* bvec64, const float* bvec32, double* out,
+                               long long spin) {
+  constexpr int RPW = 32 / LW;              // rows per warp
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int sub = lane % LW, grp = lane / LW;
   const int64_t chunk_rows = tile_rows;
   const size_t chunk_bytes = (size_t)chunk_rows * ld * 4;
   const int nst = (int)((ring_bytes / chunk_bytes) < B_STAGES ? (ring_bytes / chunk_bytes) : B_STAGES);
@@ -179,6 +189,14 @@ __device__ bool stream_pass(BShared& sh, unsigned char* ring, size_t ring_bytes,
   float acc[B_NI], cmp[B_NI];
 #pragma unroll
   for (int i = 0; i < B_NI; ++i) acc[i] = cmp[i] = 0.f;
+  // this lane's columns of p or beta (zero beyond d)
+  float pv[B_NI], blo[B_NI];
+#pragma unroll
+  for (int i = 0; i < B_NI; ++i) {
+    const int c = sub + LW * i;
+    pv[i] = (c < B_MAXD) ? (mode == 0 ? sh.pf[c] : sh.bh[c]) : 0.f;
+    blo[i] = (c < B_MAXD && mode == 2) ? sh.bl[c] : 0.f;
+  }
   bool ok = true;
   if (warp == BW) {
     if (lane == 0) {
@@ -207,31 +225,28 @@ __device__ bool stream_pass(BShared& sh, unsigned char* ring, size_t ring_bytes,
       const float* tile = reinterpret_cast<const float*>(ring + (size_t)s * chunk_bytes);
       const int64_t r0 = k * chunk_rows;
       const int64_t rows = (m - r0 < chunk_rows) ? m - r0 : chunk_rows;
-      for (int rr = warp; rr < rows; rr += BW) {
-        const float* row = tile + (size_t)rr * ld;
+      for (int64_t base = (int64_t)warp * RPW; base < rows; base += (int64_t)BW * RPW) {
+        const int64_t rr = base + grp;
+        const bool live = rr < rows;
+        const float* row = tile + (size_t)(live ? rr : 0) * ld;
         float x[B_NI];
 #pragma unroll
         for (int i = 0; i < B_NI; ++i) {
-          const int c = lane + 32 * i;
-          x[i] = (c < d) ? row[c] : 0.f;
+          const int c = sub + LW * i;
+          x[i] = (live && c < d) ? row[c] : 0.f;
         }
         if (mode == 0 || mode == 1) {
           float t = 0.f;
-          if (mode == 0) {
 #pragma unroll
-            for (int i = 0; i < B_NI; ++i) t = fmaf(x[i], sh.pf[lane + 32 * i], t);
-            t = warp_allsum(t);
-          } else {
+          for (int i = 0; i < B_NI; ++i) t = fmaf(x[i], pv[i], t);
 #pragma unroll
-            for (int i = 0; i < B_NI; ++i) t = fmaf(x[i], sh.bh[lane + 32 * i], t);
-            t = warp_allsum(t);
-            t = (float)bvec64[r0 + rr] - t;
-          }
+          for (int o = LW / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (mode == 1) t = live ? (float)bvec64[r0 + rr] - t : 0.f;
 #pragma unroll
           for (int i = 0; i < B_NI; ++i) {
-            float p, pe, s2, se;
-            two_prod(t, x[i], p, pe);
-            two_sum(acc[i], p, s2, se);
+            float pr, pe, s2, se;
+            two_prod(t, x[i], pr, pe);
+            two_sum(acc[i], pr, s2, se);
             acc[i] = s2;
             cmp[i] += pe + se;
           }
@@ -240,32 +255,32 @@ __device__ bool stream_pass(BShared& sh, unsigned char* ring, size_t ring_bytes,
           float sh_ = 0.f, sl = 0.f;
 #pragma unroll
           for (int i = 0; i < B_NI; ++i) {
-            const int c = lane + 32 * i;
-            float p, pe, s2, se;
-            two_prod(x[i], sh.bh[c], p, pe);
-            two_sum(sh_, p, s2, se);
+            float pr, pe, s2, se;
+            two_prod(x[i], pv[i], pr, pe);
+            two_sum(sh_, pr, s2, se);
             sh_ = s2;
-            sl += pe + se + x[i] * sh.bl[c];
+            sl += pe + se + x[i] * blo[i];
           }
-          // warp all-reduce of the pair (hi, lo): sum hi with TwoSum, lo plainly
+          // group all-reduce of the pair (hi, lo): hi with TwoSum, lo plainly,
+          // commutative so both partner lanes end with the same bits
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
+          for (int o = LW / 2; o > 0; o >>= 1) {
             const float oh = __shfl_xor_sync(0xffffffffu, sh_, o);
             const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
             float s2, se;
             two_sum(sh_, oh, s2, se);
             sh_ = s2;
-            sl = __fadd_rn(__fadd_rn(sl, ol), se);   // same bits in both partner lanes
+            sl = __fadd_rn(__fadd_rn(sl, ol), se);
           }
-          const float y = bvec32[r0 + rr];
+          const float y = live ? bvec32[r0 + rr] : 0.f;
           float th, tl;
           two_sum(y, -sh_, th, tl);
           tl -= sl;
 #pragma unroll
           for (int i = 0; i < B_NI; ++i) {
-            float p, pe, s2, se;
-            two_prod(th, x[i], p, pe);
-            two_sum(acc[i], p, s2, se);
+            float pr, pe, s2, se;
+            two_prod(th, x[i], pr, pe);
+            two_sum(acc[i], pr, s2, se);
             acc[i] = s2;
             cmp[i] += pe + se + tl * x[i];
           }
@@ -280,15 +295,19 @@ __device__ bool stream_pass(BShared& sh, unsigned char* ring, size_t ring_bytes,
   if (warp < BW) {
 #pragma unroll
     for (int i = 0; i < B_NI; ++i) {
-      const int c = lane + 32 * i;
-      if (c < d) sh.red[warp][c] = (double)acc[i] + (double)cmp[i];
+      double v = (double)acc[i] + (double)cmp[i];
+      // add the groups' sums of the same column (fixed xor order)
+#pragma unroll
+      for (int o = LW; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const int c = sub + LW * i;
+      if (grp == 0 && c < d) sh.red[warp][c] = v;
     }
   }
   __syncthreads();
   for (int c = tid; c < d; c += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < BW; ++w) s += sh.red[w][c];
-    out[c] = s;
+    double sacc = 0.0;
+    for (int w = 0; w < BW; ++w) sacc += sh.red[w][c];
+    out[c] = sacc;
   }
   if (tid == 0)
     for (int s = 0; s < nst; ++s) {
@@ -297,6 +316,29 @@ __device__ bool stream_pass(BShared& sh, unsigned char* ring, size_t ring_bytes,
     }
   __syncthreads();
   return ok;
+}
+
+__device__ bool stream_pass(BShared& sh, unsigned char* ring, size_t ring_bytes, const float* A,
+                            int64_t m, int64_t ld, int d, int tile_rows, int mode,
+                            const double* bvec64, const float* bvec32, double* out,
+                            long long spin) {
+  if (d <= 8)
+    return stream_pass_lw<1>(sh, ring, ring_bytes, A, m, ld, d, tile_rows, mode, bvec64, bvec32,
+                             out, spin);
+  if (d <= 16)
+    return stream_pass_lw<2>(sh, ring, ring_bytes, A, m, ld, d, tile_rows, mode, bvec64, bvec32,
+                             out, spin);
+  if (d <= 32)
+    return stream_pass_lw<4>(sh, ring, ring_bytes, A, m, ld, d, tile_rows, mode, bvec64, bvec32,
+                             out, spin);
+  if (d <= 64)
+    return stream_pass_lw<8>(sh, ring, ring_bytes, A, m, ld, d, tile_rows, mode, bvec64, bvec32,
+                             out, spin);
+  if (d <= 128)
+    return stream_pass_lw<16>(sh, ring, ring_bytes, A, m, ld, d, tile_rows, mode, bvec64, bvec32,
+                              out, spin);
+  return stream_pass_lw<32>(sh, ring, ring_bytes, A, m, ld, d, tile_rows, mode, bvec64, bvec32,
+                            out, spin);
 }
 
 // Block-wide deterministic sum of one double per thread.

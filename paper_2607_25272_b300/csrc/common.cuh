@@ -105,41 +105,58 @@ __device__ __forceinline__ float warp_allsum(float v) {
 
 // ---------------------------------------------------------------------------
 // Grid barrier of a cooperative launch (every CTA of the grid is resident).
-// bar[0] counts arrivals, bar[1] is the generation.  The last CTA to arrive
-// resets the count and advances the generation; the others wait until the
-// generation changes, at most `spin` clock cycles.  Returns false when the
-// wait expired: the status word is set to DEV_TIMEOUT and the CTA must leave
-// (the other CTAs then time out at their next barrier).  Called by every
-// thread of the CTA; *s_fail is a shared flag, 0 at kernel start.
+// bar[0] counts arrivals and bar[kBarGen] is the generation, on separate
+// 128-byte lines so that the polling does not contend with the arrivals.
+// Arrival is an acquire-release atomic add (it publishes the CTA's writes,
+// ordered before it by the CTA barrier); the last CTA to arrive resets the
+// count and releases the next generation; the others poll the generation
+// with acquire loads and a short back-off, at most `spin` clock cycles.
+// Returns false when the wait expired: the status word is set to DEV_TIMEOUT
+// and the CTA must leave (the other CTAs then time out at their next
+// barrier).  Called by every thread of the CTA; *s_fail is a shared flag, 0
+// at kernel start.
 // ---------------------------------------------------------------------------
+constexpr int kBarGen = 32;      // word index of the generation
+constexpr int kBarWords = 64;    // words a barrier occupies
+
 __device__ __forceinline__ unsigned ld_acquire_gpu_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+               : "=r"(old)
+               : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_gpu_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, int* status, long long spin,
                                                   int* s_fail) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = ld_acquire_gpu_u32(bar + 1);
-    __threadfence();
-    const unsigned prev = atomicAdd(bar, 1u);
+    unsigned* gen = bar + kBarGen;
+    const unsigned g = ld_acquire_gpu_u32(gen);
+    const unsigned prev = atom_add_acq_rel_gpu_u32(bar, 1u);
     if (prev == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+      bar[0] = 0u;                      // ordered before the release below
+      st_release_gpu_u32(gen, g + 1u);
     } else {
       const long long t0 = clock64();
-      while (ld_acquire_gpu_u32(bar + 1) == g) {
+      while (ld_acquire_gpu_u32(gen) == g) {
         if (clock64() - t0 > spin) {
           atomicExch(status, DEV_TIMEOUT);
           *s_fail = 1;
           break;
         }
+        __nanosleep(32);
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return *s_fail == 0;

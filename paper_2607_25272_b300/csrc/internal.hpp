@@ -94,7 +94,7 @@ struct Sketch {
   double* qr_red = nullptr;     // 2 x SMs x (2 x panel width): per-CTA partial sums
   double* qr_wp = nullptr;      // SMs x panel width x d: per-CTA partials of V^T C
   double* qr_wt = nullptr;      // panel width x d: T^T V^T C
-  unsigned* qr_bar = nullptr;   // grid barrier: arrival count, generation
+  unsigned* qr_bar = nullptr;   // grid barrier (kBarWords): arrival count, generation
   unsigned long long* colmax = nullptr;  // d + 1: largest |x| per column (bit pattern)
   int* colshift = nullptr;      // d + 1: fixed-point scale exponent per column
   PassGeom geom[SPCG_MAX_STAGES];  // fused-pass geometry of stage i
@@ -149,7 +149,9 @@ struct spcg_ctx {
   int prof_cap = 0;
   int prof_used = 0;
   double prof_ms = 0.0;
-  // device workspace of this context (dalloc/dfree in api.cu)
+  // device workspace of this context (dalloc/dfree in api.cu); contexts made
+  // by spcg_solve_host draw it from the library's stream-ordered pool
+  cudaMemPool_t pool = nullptr;
   size_t ws_bytes = 0;
   std::unordered_map<const void*, size_t> ws_sizes;
 };

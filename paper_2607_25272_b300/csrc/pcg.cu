@@ -57,12 +57,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
   return true;
 }
+// L2 policy for operand tiles that are read once per pass: evict first, so
+// that a pass streaming gigabytes does not push the d x d factors, the
+// per-CTA partials and the d-vectors (read between passes) out of L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
+                                            uint64_t* bar, uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
 }
 
@@ -269,6 +277,7 @@ __global__ void __launch_bounds__(PassCfg<NI, sizeof(T)>::THREADS, 1)
   if (warp == 0) {
     // ---- producer: one lane issues the TMA box loads of each row tile ----
     if (lane == 0) {
+      const uint64_t pol = l2_evict_first_policy();
       for (int k = 0; k < my_tiles; ++k) {
         const int s = k % a.stages;
         if (k >= a.stages) {
@@ -289,7 +298,7 @@ __global__ void __launch_bounds__(PassCfg<NI, sizeof(T)>::THREADS, 1)
         T* dst = tiles + (size_t)s * a.stage_elems;
         for (int bx = 0; bx < a.nbox; ++bx)
           tma_load_2d(dst + (size_t)bx * a.slot_elems, &tmap, bx * a.boxc, tile * a.tm,
-                      &full[s]);
+                      &full[s], pol);
       }
     }
   } else {
@@ -586,6 +595,7 @@ __global__ void __launch_bounds__(kPreWarps * 32)
 // ---------------------------------------------------------------------------
 constexpr int kDsThreads = 256;
 constexpr int kDsWarps = kDsThreads / 32;
+constexpr int kDsUnroll = 8;   // independent loads a lane has in flight
 
 struct DspaceArgs {
   int d;
@@ -652,7 +662,16 @@ __global__ void __launch_bounds__(kDsThreads) k_dspace(const DspaceArgs a) {
   double pw = 0.0;
   for (int j = c_lo + warp; j < c_hi; j += kDsWarps) {
     double sacc = 0.0;
-    for (int b = lane; b < a.nb; b += 32) sacc += a.partials[(size_t)b * a.ldp + j];
+    for (int b0 = 0; b0 < a.nb; b0 += 32 * kDsUnroll) {   // loads first, then the sums in order
+      double v[kDsUnroll];
+#pragma unroll
+      for (int k = 0; k < kDsUnroll; ++k) {
+        const int b = b0 + lane + 32 * k;
+        v[k] = b < a.nb ? a.partials[(size_t)b * a.ldp + j] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < kDsUnroll; ++k) sacc += v[k];
+    }
     sacc = warp_allsum(sacc);
     if (lane == 0) {
       if (a.iter) {
@@ -696,7 +715,19 @@ __global__ void __launch_bounds__(kDsThreads) k_dspace(const DspaceArgs a) {
   for (int i = gw; i < d; i += W) {
     const double* Ri = a.RinvT + (size_t)i * d;
     double sacc = 0.0;
-    for (int j = lane; j <= i; j += 32) sacc = fma(Ri[j], gs[j], sacc);
+    for (int j0 = 0; j0 <= i; j0 += 32 * kDsUnroll) {   // row entries 0..i
+      double v[kDsUnroll];
+#pragma unroll
+      for (int k = 0; k < kDsUnroll; ++k) {
+        const int j = j0 + lane + 32 * k;
+        v[k] = j <= i ? Ri[j] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < kDsUnroll; ++k) {
+        const int j = j0 + lane + 32 * k;
+        if (j <= i) sacc = fma(v[k], gs[j], sacc);
+      }
+    }
     sacc = warp_allsum(sacc);
     if (lane == 0) a.u[i] = sacc;
   }
@@ -712,9 +743,22 @@ __global__ void __launch_bounds__(kDsThreads) k_dspace(const DspaceArgs a) {
     const double* Ri = a.Rinv + (size_t)i * d;
     const double* Rr = a.R + (size_t)i * d;
     double zs = 0.0, rs = 0.0;
-    for (int j = i + lane; j < d; j += 32) {
-      zs = fma(Ri[j], us[j], zs);
-      rs = fma(Rr[j], bs[j], rs);
+    for (int j0 = i; j0 < d; j0 += 32 * kDsUnroll) {   // row entries i..d-1
+      double vz[kDsUnroll], vr[kDsUnroll];
+#pragma unroll
+      for (int k = 0; k < kDsUnroll; ++k) {
+        const int j = j0 + lane + 32 * k;
+        vz[k] = j < d ? Ri[j] : 0.0;
+        vr[k] = j < d ? Rr[j] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < kDsUnroll; ++k) {
+        const int j = j0 + lane + 32 * k;
+        if (j < d) {
+          zs = fma(vz[k], us[j], zs);
+          rs = fma(vr[k], bs[j], rs);
+        }
+      }
     }
     zs = warp_allsum(zs);
     rs = warp_allsum(rs);
@@ -1237,6 +1281,7 @@ __global__ void __launch_bounds__(DfCfg<NI>::THREADS, 1)
   int issued = 0;
   if (warp == 0) {
     if (lane == 0) {
+      const uint64_t pol = l2_evict_first_policy();
       for (int k = 0; k < my_tiles; ++k) {
         const int s = k % a.stages;
         if (k >= a.stages && !mbar_wait_bounded(&empty[s], ((k / a.stages) - 1) & 1, a.spin)) {
@@ -1250,9 +1295,10 @@ __global__ void __launch_bounds__(DfCfg<NI>::THREADS, 1)
         mbar_expect_tx(&full[s], a.tx_bytes);
         float* dst = tiles + (size_t)s * a.stage_elems;
         for (int bx = 0; bx < a.nbox; ++bx) {
-          tma_load_2d(dst + (size_t)bx * a.slot_elems, &tmh, bx * a.boxc, tile * a.tm, &full[s]);
+          tma_load_2d(dst + (size_t)bx * a.slot_elems, &tmh, bx * a.boxc, tile * a.tm, &full[s],
+                      pol);
           tma_load_2d(dst + (size_t)(a.nbox + bx) * a.slot_elems, &tml, bx * a.boxc, tile * a.tm,
-                      &full[s]);
+                      &full[s], pol);
         }
       }
     }

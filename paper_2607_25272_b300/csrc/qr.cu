@@ -190,6 +190,7 @@ constexpr int QSL = 2 * QB;            // reduction slots of a column step
 constexpr int QT = 256;                // threads per CTA
 constexpr int QLD = QB + 1;            // row stride of the panel slice in shared memory
 constexpr int QCOLB = 8;               // columns per batch in the T^T W phase
+constexpr int QUNR = 8;                // independent loads in flight per thread in the sums
 
 struct QrCoopArgs {
   double* A;           // r x d column-major (ld = r), reduced in place
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
   double* pv0 = comb + 4 * QSL;                      // QB: v_0 of the panel's reflectors
   double* wsm = pv0 + QB;                            // QCOLB x QB: W columns of one batch
   __shared__ int s_fail;
+  __shared__ double sc[2];   // v_0 and tau of the current reflector
   const int tid = threadIdx.x, G = gridDim.x, q = blockIdx.x;
   if (tid == 0) s_fail = 0;
   if (*a.status != 0) return;                        // uniform: set before this launch
@@ -266,26 +268,37 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
         // four quarter sums in order
         const int sl = tid % QSL, grp = tid / QSL;
         double acc = 0.0;
-#pragma unroll 4
-        for (int g = grp; g < G; g += 4) acc += red[(size_t)g * QSL + sl];
+        for (int g0 = grp; g0 < G; g0 += 4 * QUNR) {   // loads first, then the sums in order
+          double v[QUNR];
+#pragma unroll
+          for (int k = 0; k < QUNR; ++k) {
+            const int g = g0 + 4 * k;
+            v[k] = g < G ? red[(size_t)g * QSL + sl] : 0.0;
+          }
+#pragma unroll
+          for (int k = 0; k < QUNR; ++k) acc += v[k];
+        }
         comb[grp * QSL + sl] = acc;
       }
       __syncthreads();
       if (tid < QSL) tot[tid] = ((comb[tid] + comb[QSL + tid]) + comb[2 * QSL + tid]) + comb[3 * QSL + tid];
       __syncthreads();
-      const double s2 = tot[j], x0 = tot[QB + j];
-      const double normx = sqrt(fma(x0, x0, s2));
-      const double alpha = (x0 >= 0.0) ? -normx : normx;
-      const double v0 = x0 - alpha;
-      const double vv = fma(v0, v0, s2);
-      const double tau = vv > 0.0 ? 2.0 / vv : 0.0;
-      if (tid == 0) {
+      if (tid == 0) {   // the reflector's scalars, once per CTA (FP64 sqrt and divide are slow)
+        const double s2 = tot[j], x0 = tot[QB + j];
+        const double normx = sqrt(fma(x0, x0, s2));
+        const double alpha = (x0 >= 0.0) ? -normx : normx;
+        const double v0 = x0 - alpha;
+        const double vv = fma(v0, v0, s2);
         pv0[j] = v0;
+        sc[0] = v0;
+        sc[1] = vv > 0.0 ? 2.0 / vv : 0.0;
         if (q == 0) {
           a.Rdiag[diag] = alpha;
           a.vdiag[diag] = v0;
         }
       }
+      __syncthreads();
+      const double v0 = sc[0], tau = sc[1];
       // T(0:j, j) = -tau T(0:j, 0:j) V(:, 0:j)^T v_j, with
       // v_l^T v_j = (below the diagonal) + v_l(diag) v_0
       if (tid < j) {
@@ -350,8 +363,13 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
           const int cc = e / QB, i = e % QB;
           double acc = 0.0;
           const double* src = a.Wp + (size_t)i * d + cb + cc;
-#pragma unroll 4
-          for (int g = 0; g < G; ++g) acc += src[(size_t)g * QB * d];
+          for (int g0 = 0; g0 < G; g0 += QUNR) {
+            double v[QUNR];
+#pragma unroll
+            for (int k = 0; k < QUNR; ++k) v[k] = g0 + k < G ? src[(size_t)(g0 + k) * QB * d] : 0.0;
+#pragma unroll
+            for (int k = 0; k < QUNR; ++k) acc += v[k];
+          }
           wsm[cc * QB + i] = acc;
         }
         __syncthreads();
@@ -536,7 +554,7 @@ spcg_status launch_precond_factor(spcg_ctx* c) {
     if (per_sm < 1) coop = false;   // cannot be co-resident: use the per-column steps
   }
   if (coop) {
-    SPCG_CK(cudaMemsetAsync(s.qr_bar, 0, 2 * sizeof(unsigned), c->stream));
+    SPCG_CK(cudaMemsetAsync(s.qr_bar, 0, kBarWords * sizeof(unsigned), c->stream));
     QrCoopArgs a{};
     a.A = s.Ahat;
     a.r = r;

@@ -189,6 +189,7 @@ _SIGS = {
                                                _P, _P, _P]),
     "spcg_probe_fma_tflops": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_double), _P]),
+    "spcg_host_pool_trim": (ctypes.c_int, []),
     "spcg_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                        ctypes.c_uint64, ctypes.POINTER(Schedule),
                                        ctypes.POINTER(Opts), _P, _P, ctypes.POINTER(Info)]),
@@ -565,6 +566,11 @@ def spcg_solve_host(X_host, Y_host, seed, sched=None, opts=None, stream=None):
                                _stream_ptr(stream), ctypes.c_void_p(beta.data_ptr()),
                                ctypes.byref(info))
     return beta, info, st
+
+
+def spcg_host_pool_trim():
+    """Hand the memory spcg_solve_host keeps between calls back to the devices."""
+    _check(lib().spcg_host_pool_trim(), "spcg_host_pool_trim")
 
 
 class Batch:

@@ -80,3 +80,24 @@ def test_batched_rejects_bad_problem():
     with pytest.raises(S.SpcgError) as e:
         S.Batch([X], [Y])
     assert e.value.status == S.SPCG_E_INVALID_ARG
+
+
+def test_batched_every_row_width():
+    """Rows per warp follow d: 32, 16, 8, 4, 2 or 1 rows share a warp for d up
+    to 8, 16, 32, 64, 128 and 256; widths at and just past each boundary,
+    every problem against the oracle's OLS at 1e-6."""
+    widths = [3, 8, 9, 16, 17, 32, 33, 64, 65, 128, 129, 256]
+    rng = np.random.default_rng(77)
+    probs = []
+    for i, d in enumerate(widths):
+        N = int(rng.integers(4096, 9000))
+        X, Y, _ = scaled_columns_problem(N, d, 1e-2, 1e2, 1.0, seed=7700 + i)
+        probs.append((X.astype(np.float32), Y.astype(np.float32)))
+    Xs, Ys = to_device(probs)
+    B = S.Batch(Xs, Ys)
+    rc, st, it, ms = B.solve(13, 1e-6)
+    assert rc == S.SPCG_OK and all(v == 0 for v in st)
+    for (X, Y), beta in zip(probs, B.betas):
+        X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+        assert rel_pred_error(X64, beta.cpu().numpy(), ols(X64, Y64)) <= 1e-6, X.shape
+    B.close()
