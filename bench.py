@@ -77,7 +77,10 @@ def base_line(args, w, value_s, metric, dtype, world=1):
             "config": {"workload": w["name"]}}
 
 
-def time_solves(solver, seed, sched, steps, warmup, stream, fn=None):
+def time_solves(solver, seed, sched, steps, warmup, stream, fn=None, region=False):
+    """Mean ms per call over `steps` calls after `warmup` calls; region=True
+    brackets the timed calls with cudaProfilerStart/Stop (for ncu
+    --profile-from-start off)."""
     import torch
     fn = fn or (lambda: solver.solve(seed, sched))
     for _ in range(warmup):
@@ -85,10 +88,14 @@ def time_solves(solver, seed, sched, steps, warmup, stream, fn=None):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    if region:
+        torch.cuda.profiler.start()
     e0.record(stream)
     outs = [fn() for _ in range(steps)]
     e1.record(stream)
     torch.cuda.synchronize()
+    if region:
+        torch.cuda.profiler.stop()
     return e0.elapsed_time(e1) / steps, outs
 
 
@@ -170,8 +177,10 @@ def run_forms(args, w):
         o = S.Opts()
         o.precision = prec
         sv = S.Solver(Xd, Yd, o)
+        region = args.ncu_region is not None and name.startswith(args.ncu_region)
         ms, outs = time_solves(sv, w["seed"], sched, steps, warmup, stream,
-                               fn=lambda sv=sv: sv.solve(w["seed"], sched, raise_on_error=False))
+                               fn=lambda sv=sv: sv.solve(w["seed"], sched, raise_on_error=False),
+                               region=region)
         beta, info, st = outs[-1]
         sv.close()
         o.profile = 1
@@ -275,6 +284,7 @@ def run_batched(args, w):
         times.append(ms)
     ms_b = float(np.median(times))
     betas = [b.clone() for b in B.betas]
+    phases = batch_phase_summary(B, Xs)
     B.close()
     # the comparator: one plain FP64 spcg_solve per problem, back to back
     loop_ms = 0.0
@@ -309,11 +319,26 @@ def run_batched(args, w):
                         "max_rel_pred_error": float(max(errs)),
                         "problems_meeting_tol": int(sum(1 for e in errs if e <= w["tol"])),
                         "autotuned_chunk_bytes": tiles,
-                        "x_bytes_fp32": int(total_bytes)},
+                        "x_bytes_fp32": int(total_bytes), "phase_ms": phases},
             "loop_plain_fp64": {"s": loop_ms / 1e3,
                                 "status_ok": int(sum(1 for v in loop_status if v == 0))},
             "speedup_batched_vs_loop": loop_ms / ms_b if ms_b > 0 else None,
             "accuracy_reference": "torch.linalg.lstsq (FP64, QR) of each problem's FP32 values"}
+
+
+PHASES = ("colmax", "countsketch", "stage_matrices", "qr", "stage1", "stage2")
+
+
+def batch_phase_summary(B, Xs, sm_mhz=2032.0):
+    """Per-phase device time of the last batched solve: summed over problems
+    and for the largest problem (cycles of the SM that solved it at the
+    maximum SM clock)."""
+    cyc = np.array(B.phase_cycles(), dtype=np.float64)
+    big = int(np.argmax([X.shape[0] * X.shape[1] for X in Xs]))
+    to_ms = 1.0 / (sm_mhz * 1e3)
+    return {"sum_over_problems": {k: float(v) for k, v in zip(PHASES, cyc.sum(0) * to_ms)},
+            "largest_problem": {"N": int(Xs[big].shape[0]), "d": int(Xs[big].shape[1]),
+                                **{k: float(v) for k, v in zip(PHASES, cyc[big] * to_ms)}}}
 
 
 def run_learned(args, w):
@@ -630,6 +655,7 @@ def run_sketch_only(args, w, local_rank):
     o.fwht_tile = args.fwht_tile
     o.fwht_first_levels = args.fwht_first
     o.qr_by_column = args.qr_by_column
+    o.qr_panel_ctas = args.qr_panel_ctas
     s = S.Solver(X, Y, o)
     sc = S.spcg_default_schedule(m, d)
     for _ in range(args.warmup):
@@ -645,6 +671,7 @@ def run_sketch_only(args, w, local_rank):
     torch.cuda.synchronize()
     print(json.dumps({"kernel": "spcg_sketch", "rows": m, "d": d, "fwht_tile": args.fwht_tile,
                       "fwht_first_levels": args.fwht_first, "qr_by_column": args.qr_by_column,
+                      "qr_panel_ctas": args.qr_panel_ctas,
                       "ms_per_call": e0.elapsed_time(e1) / args.steps}), flush=True)
     s.close()
 
@@ -702,7 +729,8 @@ def run_batched_only(args, w, local_rank):
     nbytes = sum(X.shape[0] * X.shape[1] * 4 for X in Xs)
     print(json.dumps({"kernel": "k_batched_spcg", "problems": args.batch,
                       "ms_per_call": float(np.median(times)), "status_ok": sum(v == 0 for v in st),
-                      "x_bytes_fp32": nbytes, "stage2_iters_sum": int(sum(it))}), flush=True)
+                      "x_bytes_fp32": nbytes, "stage2_iters_sum": int(sum(it)),
+                      "phase_ms": batch_phase_summary(B, Xs)}), flush=True)
     B.close()
 
 
@@ -916,6 +944,8 @@ def main():
                     help="spcg_opts.fwht_first_levels for --kernel sketch")
     ap.add_argument("--qr-by-column", type=int, default=0,
                     help="spcg_opts.qr_by_column for --kernel sketch")
+    ap.add_argument("--qr-panel-ctas", type=int, default=0,
+                    help="spcg_opts.qr_panel_ctas for --kernel sketch")
     ap.add_argument("--pass-dtype", default="float64",
                     choices=["float64", "float32", "bfloat16", "pair"])
     args = ap.parse_args()

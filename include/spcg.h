@@ -136,7 +136,9 @@ typedef struct {
                                per-round pass kernel; all give the same bits  */
   int32_t fwht_first_levels; /* levels of the first of two transform passes;
                                0 = split evenly                               */
-  int32_t reserved;         /* set to 0                                         */
+  int32_t qr_panel_ctas;    /* CTAs that factor each 32-column panel of the
+                               preconditioner QR; 0 = about one per 48 rows of
+                               the sketch (at most one per SM)                 */
 } spcg_opts;
 
 /* Stage II operand of the mixed path (spcg_opts.inner_prec, spcg_info.inner_prec).
@@ -280,6 +282,35 @@ spcg_status spcg_refine(spcg_ctx* ctx, double tol, int32_t max_iters,
  */
 spcg_status spcg_solve(spcg_ctx* ctx, uint64_t seed, const spcg_schedule* sched,
                        double* beta, spcg_info* info);
+
+/*
+ * Capture-safe Stage I + Stage II: enqueue every launch of the solve on the
+ * context's stream without reading anything back, so that the sequence can be
+ * captured into a CUDA graph and replayed.  Requires a prior spcg_sketch
+ * (which synchronises; call it outside the capture).  beta (device, d, output)
+ * is set to 0 and run through all K stages; Stage II then runs `rounds`
+ * rounds of [true gradient X^T (Y - X beta) and the stopping test; at most
+ * iters_per_round PCG iterations with the recursive test], then one more
+ * true-gradient test.  The stopping state lives on the device: once the
+ * recursive test holds, the rest of a round does nothing; the next true
+ * gradient either confirms it (every later launch then does nothing) or the
+ * iterations go on from it.  The schedule is sized by the caller: rounds
+ * bounds the restarts, rounds x iters_per_round the Stage II iterations.
+ * spcg_opts.profile must be 0.  Nothing is allocated.
+ * Errors: SPCG_E_INVALID_ARG, SPCG_E_STATE (no sketch), SPCG_E_CUDA.
+ */
+spcg_status spcg_solve_enqueue(spcg_ctx* ctx, double* beta, int32_t rounds,
+                               int32_t iters_per_round);
+
+/*
+ * The outcome of the last spcg_solve_enqueue sequence (synchronises the
+ * stream): SPCG_OK when the stopping rule was confirmed on a true gradient,
+ * SPCG_E_NOT_CONVERGED when the schedule ran out first, or the device error
+ * (SPCG_E_BREAKDOWN, SPCG_E_TIMEOUT).  info (host, may be NULL):
+ * refine_iters = Stage II iterations that ran, converged, sqrt_gamma,
+ * norm_R_beta, the precision choices; launch counts are those enqueued.
+ */
+spcg_status spcg_solve_result(spcg_ctx* ctx, spcg_info* info);
 
 /*
  * Algorithm 1 end to end from HOST memory: copies X and Y to the device,
@@ -476,6 +507,21 @@ void spcg_batch_destroy(spcg_batch* b);
  */
 spcg_status spcg_batch_solve(spcg_batch* b, uint64_t seed, double tol, int32_t* status_out,
                              int32_t* iters_out, double* ms_out);
+
+/* The whole batch in one call: spcg_batch_create, spcg_batch_solve,
+ * spcg_batch_destroy (the per-CTA scratch is allocated and freed inside).
+ * status_out, iters_out: host arrays of n, may be NULL.  Returns the first
+ * non-zero per-problem status, or the error of a failed create. */
+spcg_status spcg_solve_batched(const spcg_problem_f32* probs, int32_t n, uint64_t seed,
+                               double tol, void* stream, int32_t* status_out,
+                               int32_t* iters_out);
+
+/* Clock cycles (of the SM that solved it) spent by each problem of the last
+ * spcg_batch_solve in its phases: [0] column maxima, [1] CountSketch buckets,
+ * [2] stage matrices, [3] preconditioner QR and R^{-1}, [4] Stage I, [5] Stage
+ * II; [6], [7] zero.  cycles_out: host, 8 n int64 in the order of the problems
+ * given to spcg_batch_create. */
+spcg_status spcg_batch_phase_cycles(spcg_batch* b, int64_t* cycles_out);
 
 /* Rows per streamed chunk, as chunk bytes per width class (d <= 32, <= 64,
  * <= 128, <= 256): 0 = 16 KB, else a multiple of 16 in [1024, 16384]. */

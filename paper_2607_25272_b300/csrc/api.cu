@@ -57,7 +57,8 @@ static spcg_status qr_alloc(spcg_ctx* c) {
   SPCG_TRY(dalloc(c, &s.qr_red, (size_t)2 * G * 2 * kQrPanel));
   SPCG_TRY(dalloc(c, &s.qr_wp, (size_t)G * kQrPanel * d));
   SPCG_TRY(dalloc(c, &s.qr_wt, (size_t)kQrPanel * d));
-  SPCG_TRY(dalloc(c, &s.qr_bar, (size_t)kBarWords));
+  SPCG_TRY(dalloc(c, &s.qr_tg, (size_t)kQrPanel * kQrPanel));
+  SPCG_TRY(dalloc(c, &s.qr_bar, (size_t)2 * kBarWords));
   return SPCG_OK;
 }
 
@@ -182,7 +183,7 @@ static spcg_status iteration(spcg_ctx* c, const Operand& op, double* beta, int& 
 
 static spcg_status run_stage(spcg_ctx* c, int i, int a_i, double* beta) {
   const PassGeom& g = c->sk.geom[i];
-  SPCG_TRY(launch_reset_flags(c));
+  SPCG_TRY(launch_reset_loop(c));
   int cur = 0, pp = 0, gp = 0;
   SPCG_TRY(start_sequence(c, g, c->sk.bK + c->sk.stage_off[i], beta, cur));
   const Operand op{&g, nullptr};
@@ -197,7 +198,7 @@ static spcg_status run_stage_m(spcg_ctx* c, int64_t m, int a_i, double* beta) {
     SPCG_TRY(make_pass_geom_t(c->sk.AK16, m, c->d, c->sk.ldak16, DT_BF16, &g));
   else
     SPCG_TRY(make_pass_geom(c->sk.AK, m, c->d, c->sk.ldak, &g));
-  SPCG_TRY(launch_reset_flags(c));
+  SPCG_TRY(launch_reset_loop(c));
   int cur = 0, pp = 0, gp = 0;
   SPCG_TRY(start_sequence(c, g, c->sk.bK, beta, cur));
   const Operand op{&g, nullptr};
@@ -247,14 +248,14 @@ static spcg_status run_refine(spcg_ctx* c, double tol, int max_iters, int max_re
     gi = c->inner_used == SPCG_INNER_DF ? Operand{&c->gxdf, &c->tml} : Operand{&c->gxf, nullptr};
   }
   int total = 0, restarts = 0;
-  SPCG_TRY(launch_reset_flags(c));
+  SPCG_TRY(launch_reset_loop(c));
   for (;;) {
     // true gradient and the stopping test on it
     int cur = 0, pp = 0, gp = 0;
     SPCG_TRY(start_sequence(c, g, c->Y, beta, cur, df_grad));
     SPCG_TRY(launch_check(c, tau));
     SPCG_TRY(sync_scalars(c));
-    if (c->host_scal.done) {
+    if (c->host_scal.done == 2) {
       res->iters = total;
       res->restarts = restarts;
       res->converged = 1;
@@ -272,8 +273,8 @@ static spcg_status run_refine(spcg_ctx* c, double tol, int max_iters, int max_re
       }
       SPCG_TRY(sync_scalars(c));
       total += c->host_scal.iters;
-      SPCG_TRY(launch_reset_flags(c));   // clears done and the iteration count
-      if (c->host_scal.done) {
+      SPCG_TRY(launch_reset_loop(c));   // clears done and the iteration count
+      if (c->host_scal.done == 1) {
         hit = true;
         break;
       }
@@ -473,7 +474,8 @@ static spcg_status create_impl(const double* X, const double* Y, int64_t N, int3
   if (c->opts.precision != SPCG_PREC_FP64 && c->opts.precision != SPCG_PREC_MIXED)
     return fail(SPCG_E_INVALID_ARG);
   if (c->opts.fwht_tile < 0 || c->opts.fwht_tile > 3 || c->opts.fwht_first_levels < 0 ||
-      c->opts.fwht_first_levels > 12 || c->opts.max_workspace_bytes < 0)
+      c->opts.fwht_first_levels > 12 || c->opts.max_workspace_bytes < 0 ||
+      c->opts.qr_panel_ctas < 0)
     return fail(SPCG_E_INVALID_ARG);
   if (c->opts.precision == SPCG_PREC_MIXED) {
     c->ldxf = (d + 3) & ~int64_t(3);
@@ -514,6 +516,7 @@ extern "C" void spcg_destroy(spcg_ctx* c) {
   dfree(c, c->sk.qr_wp);
   dfree(c, c->sk.qr_wt);
   dfree(c, c->sk.qr_bar);
+  dfree(c, c->sk.qr_tg);
   dfree(c, c->mlp_x);
   dfree(c, c->mlp_y);
   dfree(c, c->feat_part);
@@ -634,6 +637,7 @@ extern "C" spcg_status spcg_pcg_stage(spcg_ctx* c, int32_t i, int32_t a_i, doubl
   if (!c || !beta) return SPCG_E_INVALID_ARG;
   if (!c->sk.ready) return SPCG_E_STATE;
   if (i < 0 || i >= c->sk.sched.K || a_i < 0) return SPCG_E_INVALID_ARG;
+  SPCG_TRY(launch_reset_flags(c));   // a new call starts without an earlier error
   SPCG_TRY(run_stage(c, i, a_i, beta));
   return sync_scalars(c);
 }
@@ -643,6 +647,7 @@ extern "C" spcg_status spcg_refine(spcg_ctx* c, double tol, int32_t max_iters, d
   if (!c || !beta || !(tol > 0.0) || max_iters < 0) return SPCG_E_INVALID_ARG;
   if (!c->sk.ready) return SPCG_E_STATE;
   if (c->opts.precision == SPCG_PREC_MIXED) SPCG_TRY(launch_to_f32(c));
+  SPCG_TRY(launch_reset_flags(c));   // a new call starts without an earlier error
   RefineResult rr;
   spcg_status st = run_refine(c, tol, max_iters, c->sk.sched.max_restarts, beta, &rr);
   if (iters_out) *iters_out = rr.iters;
@@ -699,6 +704,69 @@ extern "C" spcg_status spcg_solve(spcg_ctx* c, uint64_t seed, const spcg_schedul
     info->ms_refine = ms;
   }
   return st;
+}
+
+extern "C" spcg_status spcg_solve_enqueue(spcg_ctx* c, double* beta, int32_t rounds,
+                                          int32_t iters_per_round) {
+  if (!c || !beta || rounds < 1 || iters_per_round < 1) return SPCG_E_INVALID_ARG;
+  if (!c->sk.ready) return SPCG_E_STATE;
+  if (c->opts.profile) return SPCG_E_INVALID_ARG;   // event timing reads the host between launches
+  const spcg_schedule& sc = c->sk.sched;
+  const bool mixed = c->opts.precision == SPCG_PREC_MIXED;
+  reset_accounting(c);
+  if (mixed) SPCG_TRY(launch_to_f32(c));
+  SPCG_TRY(launch_reset_flags(c));
+  SPCG_CK(cudaMemsetAsync(beta, 0, (size_t)c->d * 8, c->stream));
+  for (int i = 0; i < sc.K; ++i) SPCG_TRY(run_stage(c, i, sc.a[i], beta));
+  // Stage II on a fixed schedule: every round is a true gradient with its
+  // test, then iters_per_round iterations with the recursive test.  Once the
+  // test passes, the rest of the round does nothing (done 1) until the next
+  // round's true gradient confirms it (done 2: everything after does nothing)
+  // or sends the iterations on from that gradient (done 0).
+  const double tau = sc.tol / 2.0;
+  c->inner_used = 0;
+  c->grad_used = choose_grad(c, sc.tol);
+  Operand gi{&c->gx, nullptr};
+  if (mixed) {
+    c->inner_used = choose_inner(c);
+    gi = c->inner_used == SPCG_INNER_DF ? Operand{&c->gxdf, &c->tml} : Operand{&c->gxf, nullptr};
+  }
+  SPCG_TRY(launch_reset_loop(c));
+  for (int rd = 0; rd < rounds; ++rd) {
+    int cur = 0, pp = 0, gp = 0;
+    SPCG_TRY(start_sequence(c, c->gx, c->Y, beta, cur, c->grad_used == SPCG_GRAD_DF));
+    SPCG_TRY(launch_check(c, tau));
+    for (int k = 0; k < iters_per_round; ++k)
+      SPCG_TRY(iteration(c, gi, beta, cur, pp, gp, k == 0, 1, tau));
+  }
+  // a last true gradient and test, so that an iterate reached in the last
+  // round can still be confirmed
+  int cur = 0;
+  SPCG_TRY(start_sequence(c, c->gx, c->Y, beta, cur, c->grad_used == SPCG_GRAD_DF));
+  SPCG_TRY(launch_check(c, tau));
+  return SPCG_OK;
+}
+
+extern "C" spcg_status spcg_solve_result(spcg_ctx* c, spcg_info* info) {
+  if (!c) return SPCG_E_INVALID_ARG;
+  const spcg_status st = sync_scalars(c);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->K = c->sk.sched.K;
+    for (int i = 0; i < c->sk.sched.K; ++i) info->stage_iters[i] = c->sk.sched.a[i];
+    info->refine_iters = c->host_scal.iters;
+    info->converged = c->host_scal.done == 2 ? 1 : 0;
+    info->sqrt_gamma = c->host_scal.sqrt_gamma;
+    info->norm_R_beta = c->host_scal.norm_rb;
+    info->cond_est = c->cond_est;
+    info->inner_prec = c->inner_used;
+    info->grad_prec = c->grad_used;
+    info->pass_launches = (int32_t)c->n_pass;
+    info->launches = (int32_t)c->n_launch;
+    info->bytes_pass = c->pass_bytes;
+  }
+  if (st != SPCG_OK) return st;
+  return c->host_scal.done == 2 ? SPCG_OK : SPCG_E_NOT_CONVERGED;
 }
 
 extern "C" spcg_status spcg_solve_host(const double* X, const double* Y, int64_t N, int32_t d,
@@ -941,6 +1009,7 @@ static spcg_status solve_choice(spcg_ctx* c, uint64_t seed, const uint16_t* Wb, 
   }
   SPCG_CK(cudaEventRecord(c->ev[1], c->stream));
   SPCG_CK(cudaMemsetAsync(c->beta_work, 0, (size_t)c->d * 8, c->stream));
+  SPCG_TRY(launch_reset_flags(c));   // the reused sketch may follow a failed call
   int idx = paper;
   spcg_schedule cand = sc;
   if (sc.K > 0) {

@@ -33,6 +33,7 @@ constexpr int BT = 32 * (BW + 1);         // + one producer warp
 constexpr int B_STAGES = 6;
 constexpr int B_MAXD = 256;
 constexpr int B_NI = B_MAXD / 32;         // columns per lane
+constexpr int B_RU = 4;                   // rows (or elements) a thread loads at once outside the ring
 
 struct BatchProblemDev {
   const float* X;
@@ -64,6 +65,8 @@ struct BatchArgs {
   int max_iters;
   int max_restarts;
   long long spin;
+  int64_t max_n;            // rows of the largest problem (row lists)
+  long long* phase_cycles;  // n x 8 clock cycles per phase of each problem, or null
 };
 
 // ---------------- small helpers ----------------
@@ -110,21 +113,75 @@ __device__ __forceinline__ void b_bulk(void* dst, const void* src, uint32_t byte
       : "memory");
 }
 
-__device__ __forceinline__ long long b_fixed(double x, int s) {
-  const long long b = __double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FF);
-  if (e == 0) return 0;
-  const unsigned long long mant = (unsigned long long)(b & 0xFFFFFFFFFFFFFll) | (1ull << 52);
-  const int sh = e - 1075 + s;
-  unsigned long long q;
-  if (sh >= 0) q = mant << sh;
-  else if (sh > -64) q = (mant + (1ull << (-sh - 1))) >> (-sh);
+// Exact conversions between FP32 values and 64-bit fixed point with integer
+// operations only (the FP64 pipe of this GPU is slow).  q = x 2^s rounded half
+// away from zero, from the FP32 bit pattern (subnormals included).
+__device__ __forceinline__ long long fixed_from_f32(float x, int s) {
+  const uint32_t b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xFFu);
+  uint64_t m = b & 0x7FFFFFu;
+  int E;                      // x = m 2^E
+  if (e == 0) {
+    if (m == 0) return 0;
+    E = -149;
+  } else {
+    m |= 0x800000u;
+    E = e - 150;
+  }
+  const int sh = E + s;
+  uint64_t q;
+  if (sh >= 0) q = m << sh;                         // the scale keeps q below 2^62
+  else if (sh > -40) q = (m + (1ull << (-sh - 1))) >> (-sh);
   else q = 0;
-  return (b < 0) ? -(long long)q : (long long)q;
+  return (b >> 31) ? -(long long)q : (long long)q;
 }
-__device__ __forceinline__ double b_unfixed(long long q, int s) {
-  // exact enough here: |q| < 2^62, one rounding to FP64 then an exact scaling
-  return ldexp((double)q, -s);
+
+// |q| 2^-s with the 53 (FP64) or 24 (FP32) leading bits, round to nearest
+// even; results below the normal range flush to zero.
+__device__ __forceinline__ void fixed_split(long long q, int s, int mbits, uint32_t& sign,
+                                            uint64_t& mant, int& exp2) {
+  sign = q < 0 ? 1u : 0u;
+  const uint64_t v = sign ? (uint64_t)(-q) : (uint64_t)q;
+  int top = 63 - __clzll((long long)v);
+  uint64_t m;
+  if (top < mbits) {
+    m = v << (mbits - 1 - top);
+  } else {
+    const int drop = top - (mbits - 1);
+    m = v >> drop;
+    const uint64_t rem = drop > 0 ? v & ((1ull << drop) - 1) : 0, half = drop > 0 ? 1ull << (drop - 1) : 0;
+    if (drop > 0 && (rem > half || (rem == half && (m & 1ull)))) ++m;
+    if (m == (1ull << mbits)) {
+      m >>= 1;
+      ++top;
+    }
+  }
+  mant = m;
+  exp2 = top - s;             // value = m 2^(exp2 - (mbits - 1))
+}
+
+__device__ __forceinline__ float f32_from_fixed(long long q, int s) {
+  if (q == 0) return 0.f;
+  uint32_t sign;
+  uint64_t m;
+  int e2;
+  fixed_split(q, s, 24, sign, m, e2);
+  const int biased = e2 + 127;
+  if (biased <= 0) return 0.f;
+  if (biased >= 255) return __uint_as_float((sign << 31) | 0x7F800000u);
+  return __uint_as_float((sign << 31) | ((uint32_t)biased << 23) | (uint32_t)(m & 0x7FFFFFu));
+}
+
+__device__ __forceinline__ double f64_from_fixed(long long q, int s) {
+  if (q == 0) return 0.0;
+  uint32_t sign;
+  uint64_t m;
+  int e2;
+  fixed_split(q, s, 53, sign, m, e2);
+  const int biased = e2 + 1023;
+  if (biased <= 0) return 0.0;
+  return __longlong_as_double((long long)(((uint64_t)sign << 63) | ((uint64_t)biased << 52) |
+                                          (m & 0xFFFFFFFFFFFFFull)));
 }
 
 // double-FP32 helpers (error-free transformations); the _rn intrinsics keep
@@ -148,7 +205,7 @@ struct BShared {
   double red[BW][B_MAXD];     // per-warp partial sums
   double scal[8];
   int colshift[B_MAXD + 1];
-  unsigned long long colmax[B_MAXD + 1];
+  uint32_t colmax32[B_MAXD + 1];    // largest |x| per column, FP32 bit pattern
   int flag;
 };
 
@@ -396,6 +453,10 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
   float* R = Ahat + (size_t)a.max_r * B_MAXD;
   float* Rinv = R + B_MAXD * B_MAXD;
   float* RinvT = Rinv + B_MAXD * B_MAXD;
+  int* cnt = reinterpret_cast<int*>(RinvT + B_MAXD * B_MAXD);   // bucket sizes, then offsets
+  int* cur = cnt + a.max_rows_int;                              // bucket fill cursors
+  int32_t* rlist = cur + a.max_rows_int;                        // row lists (2 x max_n)
+  __shared__ int sh_scan[BT];
 
   for (;;) {
     if (tid == 0) s_p = atomicAdd(a.queue, 1);
@@ -413,44 +474,157 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
     const uint64_t key = a.seed + (uint64_t)p;
     int status = 0;
 
-    // 1. column maxima -> fixed-point scales
-    for (int c = tid; c < C; c += blockDim.x) sh.colmax[c] = 0ull;
+    long long t_phase = clock64();
+    auto phase_mark = [&](int k) {
+      if (a.phase_cycles && tid == 0) {
+        const long long t = clock64();
+        a.phase_cycles[(size_t)p * 8 + k] = t - t_phase;
+        t_phase = t;
+      }
+    };
+    // 1. column maxima of |[X Y]| (FP32 bit patterns: integer order is numeric
+    //    order for non-negative floats) -> fixed-point scales
+    for (int c = tid; c < C; c += blockDim.x) sh.colmax32[c] = 0u;
     __syncthreads();
-    for (int64_t i = warp; i < N; i += nw) {
-      for (int c = lane; c < C; c += 32) {
-        const float v = (c < d) ? P.X[i * ldx + c] : P.Y[i];
-        atomicMax(&sh.colmax[c], (unsigned long long)__double_as_longlong(fabs((double)v)));
+    {
+      uint32_t mx[(B_MAXD + 1 + 31) / 32];
+#pragma unroll
+      for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) mx[u] = 0u;
+      // B_RU rows per warp and step, all loads issued before the maxima
+      for (int64_t i0 = (int64_t)warp * B_RU; i0 < N; i0 += (int64_t)nw * B_RU) {
+        float v[B_RU][(B_MAXD + 1 + 31) / 32];
+#pragma unroll
+        for (int q = 0; q < B_RU; ++q)
+#pragma unroll
+          for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
+            const int c = lane + 32 * u;
+            const int64_t i = i0 + q;
+            v[q][u] = (c < C && i < N) ? ((c < d) ? P.X[i * ldx + c] : P.Y[i]) : 0.f;
+          }
+#pragma unroll
+        for (int q = 0; q < B_RU; ++q)
+#pragma unroll
+          for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
+            const uint32_t bits = __float_as_uint(v[q][u]) & 0x7FFFFFFFu;
+            mx[u] = bits > mx[u] ? bits : mx[u];
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
+        const int c = lane + 32 * u;
+        if (c < C && mx[u]) atomicMax(&sh.colmax32[c], mx[u]);
       }
     }
     __syncthreads();
     for (int c = tid; c < C; c += blockDim.x) {
-      const int e = (int)((sh.colmax[c] >> 52) & 0x7FF);
-      sh.colshift[c] = (e == 0) ? 0 : 61 - nbits - (e - 1023);
+      // s_c = 61 - n - E_c with 2^{E_c} <= max_c < 2^{E_c+1}: every sum of
+      // N' <= 2^n terms stays below 2^62
+      const uint32_t bits = sh.colmax32[c];
+      const int e = (int)(bits >> 23);
+      int E = 0;
+      if (e > 0) E = e - 127;
+      else if (bits) E = (31 - __clz((int)bits)) - 149;
+      sh.colshift[c] = bits == 0 ? 0 : 61 - nbits - E;
     }
-    // 2. scatter into m_K + r buckets
+    phase_mark(0);
+    // 2. CountSketch by gathering: bucket sizes (one integer atomic per row and
+    //    sketch, on arrays small enough to stay in L2), offsets, a row list
+    //    per bucket, then every bucket sums its rows in 64-bit registers and
+    //    is written once.  Integer sums: the order of the rows in a bucket
+    //    does not change a bit.
     const int64_t nb = mK + r;
-    for (int64_t e = tid; e < nb * C; e += blockDim.x) buckets[e] = 0;
+    for (int64_t e = tid; e < nb; e += blockDim.x) cnt[e] = 0;
     __syncthreads();
-    long long* hatb = buckets + mK * C;
-    for (int64_t j = warp; j < N; j += nw) {
+    for (int64_t j = tid; j < N; j += blockDim.x) {
       const u32x4 w = philox10(u32x4{(uint32_t)j, (uint32_t)((uint64_t)j >> 32), 4u, 0u}, key);
       const u32x4 wh = philox10(u32x4{(uint32_t)j, (uint32_t)((uint64_t)j >> 32), 5u, 0u}, key);
-      const int64_t b = mK > 0 ? (int64_t)(w.x & (uint32_t)(mK - 1)) : 0;
-      const int64_t bh = (int64_t)(((uint64_t)wh.x * (uint64_t)r) >> 32);
-      const bool neg = w.y & 1u, negh = wh.y & 1u;
-      for (int c = lane; c < C; c += 32) {
-        const double v = (c < d) ? (double)P.X[j * ldx + c] : (double)P.Y[j];
-        const long long q = b_fixed(v, sh.colshift[c]);
-        if (mK > 0)
-          atomicAdd(reinterpret_cast<unsigned long long*>(buckets + b * C + c),
-                    (unsigned long long)(neg ? -q : q));
-        if (c < d)
-          atomicAdd(reinterpret_cast<unsigned long long*>(hatb + bh * C + c),
-                    (unsigned long long)(negh ? -q : q));
+      if (mK > 0) atomicAdd(&cnt[w.x & (uint32_t)(mK - 1)], 1);
+      atomicAdd(&cnt[mK + (int64_t)(((uint64_t)wh.x * (uint64_t)r) >> 32)], 1);
+    }
+    __syncthreads();
+    {
+      // exclusive scan of cnt[0, nb) (stage buckets, then preconditioner
+      // buckets, so those offsets start at N): per-thread chunks, then the
+      // chunk totals
+      const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+      const int64_t lo = (int64_t)tid * per, hi = lo + per < nb ? lo + per : nb;
+      int tsum = 0;
+      for (int64_t e = lo; e < hi; ++e) tsum += cnt[e];
+      sh_scan[tid] = tsum;
+      __syncthreads();
+      if (tid == 0) {
+        int run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+          const int v = sh_scan[k];
+          sh_scan[k] = run;
+          run += v;
+        }
+      }
+      __syncthreads();
+      int run = sh_scan[tid];
+      for (int64_t e = lo; e < hi; ++e) {
+        const int v = cnt[e];
+        cnt[e] = run;
+        cur[e] = run;
+        run += v;
       }
     }
     __syncthreads();
-    // 3. stage matrices by folding, and the preconditioner sketch (column-major)
+    for (int64_t j = tid; j < N; j += blockDim.x) {
+      const u32x4 w = philox10(u32x4{(uint32_t)j, (uint32_t)((uint64_t)j >> 32), 4u, 0u}, key);
+      const u32x4 wh = philox10(u32x4{(uint32_t)j, (uint32_t)((uint64_t)j >> 32), 5u, 0u}, key);
+      if (mK > 0) {
+        const int slot = atomicAdd(&cur[w.x & (uint32_t)(mK - 1)], 1);
+        rlist[slot] = (int32_t)((uint32_t)j | ((w.y & 1u) << 31));
+      }
+      const int slot = atomicAdd(&cur[mK + (int64_t)(((uint64_t)wh.x * (uint64_t)r) >> 32)], 1);
+      rlist[slot] = (int32_t)((uint32_t)j | ((wh.y & 1u) << 31));
+    }
+    __syncthreads();
+    // bucket sums: a warp per bucket, lanes over the columns of each row, the
+    // loads of B_RU rows of the bucket issued before their sums
+    for (int64_t t = warp; t < nb; t += nw) {
+      const bool hat = t >= mK;
+      long long acc[(B_MAXD + 1 + 31) / 32];
+#pragma unroll
+      for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) acc[u] = 0;
+      const int k1 = cur[t];
+      for (int k0 = cnt[t]; k0 < k1; k0 += B_RU) {
+        float v[B_RU][(B_MAXD + 1 + 31) / 32];
+        uint32_t ent[B_RU];
+#pragma unroll
+        for (int q = 0; q < B_RU; ++q) ent[q] = k0 + q < k1 ? (uint32_t)rlist[k0 + q] : 0u;
+#pragma unroll
+        for (int q = 0; q < B_RU; ++q) {
+          const int64_t j = ent[q] & 0x7FFFFFFFu;
+#pragma unroll
+          for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
+            const int c = lane + 32 * u;
+            v[q][u] = (c < C && k0 + q < k1) ? ((c < d) ? P.X[j * ldx + c] : P.Y[j]) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < B_RU; ++q)
+#pragma unroll
+          for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
+            const int c = lane + 32 * u;
+            if (c < C) {
+              const long long fq = fixed_from_f32(v[q][u], sh.colshift[c]);
+              acc[u] += (ent[q] >> 31) ? -fq : fq;   // rows past the bucket hold 0
+            }
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
+        const int c = lane + 32 * u;
+        if (c >= C) continue;
+        if (!hat) buckets[t * C + c] = acc[u];
+        else if (c < d) Ahat[(int64_t)c * r + (t - mK)] = f32_from_fixed(acc[u], sh.colshift[c]);
+      }
+    }
+    __syncthreads();
+    phase_mark(1);
+    // 3. stage matrices by folding the buckets modulo m_i (integer adds)
     int64_t off[SPCG_MAX_STAGES];
     {
       int64_t o = 0;
@@ -459,29 +633,53 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
         o += P.m[i];
       }
     }
-    for (int64_t e = tid; e < r * d; e += blockDim.x) {
-      const int64_t t = e / d;
-      const int c = (int)(e % d);
-      Ahat[(int64_t)c * r + t] = (float)b_unfixed(hatb[t * C + c], sh.colshift[c]);
-    }
-    int64_t cur = mK;
+    int64_t cur_m = mK;
     for (int i = K - 1; i >= 0; --i) {
-      while (cur > P.m[i]) {
-        cur >>= 1;
-        for (int64_t e = tid; e < cur * C; e += blockDim.x) buckets[e] += buckets[e + cur * C];
+      while (cur_m > P.m[i]) {
+        cur_m >>= 1;
+        const int64_t ne = cur_m * C;
+        for (int64_t e0 = tid; e0 < ne; e0 += (int64_t)blockDim.x * 2 * B_RU) {   // loads in flight
+          long long hi[2 * B_RU], lo[2 * B_RU];
+#pragma unroll
+          for (int q = 0; q < 2 * B_RU; ++q) {
+            const int64_t e = e0 + (int64_t)q * blockDim.x;
+            hi[q] = e < ne ? buckets[e + ne] : 0;
+            lo[q] = e < ne ? buckets[e] : 0;
+          }
+#pragma unroll
+          for (int q = 0; q < 2 * B_RU; ++q) {
+            const int64_t e = e0 + (int64_t)q * blockDim.x;
+            if (e < ne) buckets[e] = lo[q] + hi[q];
+          }
+        }
         __syncthreads();
       }
       float* S_i = stages + off[i] * ld;
       double* b_i = bst + off[i];
-      for (int64_t e = tid; e < cur * ld; e += blockDim.x) {
-        const int64_t t = e / ld;
-        const int c = (int)(e % ld);
-        S_i[e] = (c < d) ? (float)b_unfixed(buckets[t * C + c], sh.colshift[c]) : 0.f;
-        if (c == 0) b_i[t] = b_unfixed(buckets[t * C + d], sh.colshift[d]);
+      const int64_t ne = cur_m * ld;
+      for (int64_t e0 = tid; e0 < ne; e0 += (int64_t)blockDim.x * B_RU) {
+        long long qv[B_RU];
+#pragma unroll
+        for (int q = 0; q < B_RU; ++q) {
+          const int64_t e = e0 + (int64_t)q * blockDim.x;
+          const int64_t t = e / ld;
+          const int c = (int)(e % ld);
+          qv[q] = (e < ne && c < d) ? buckets[t * C + c] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < B_RU; ++q) {
+          const int64_t e = e0 + (int64_t)q * blockDim.x;
+          if (e >= ne) continue;
+          const int64_t t = e / ld;
+          const int c = (int)(e % ld);
+          S_i[e] = (c < d) ? f32_from_fixed(qv[q], sh.colshift[c]) : 0.f;
+          if (c == 0) b_i[t] = f64_from_fixed(buckets[t * C + d], sh.colshift[d]);
+        }
       }
       __syncthreads();
     }
     __syncthreads();
+    phase_mark(2);
     // 4. Householder QR of S-hat X (FP32), R with positive diagonal, R^{-1}
     for (int k = 0; k < d; ++k) {
       float* colk = Ahat + (int64_t)k * r;
@@ -498,12 +696,28 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
         const float tau = (float)(2.0 / vv), v0f = (float)v0;
         for (int j = k + 1 + warp; j < d; j += nw) {
           float* cj = Ahat + (int64_t)j * r;
-          float s = 0.f;
-          for (int64_t i = k + 1 + lane; i < r; i += 32) s = fmaf(colk[i], cj[i], s);
-          s = warp_allsum(s) + v0f * cj[k];
-          const float f = tau * s;
+          // four independent partial sums: four pairs of loads in flight
+          float s0 = 0.f, s1 = 0.f, s2f = 0.f, s3 = 0.f;
+          int64_t i = k + 1 + lane;
+          for (; i + 96 < r; i += 128) {
+            s0 = fmaf(colk[i], cj[i], s0);
+            s1 = fmaf(colk[i + 32], cj[i + 32], s1);
+            s2f = fmaf(colk[i + 64], cj[i + 64], s2f);
+            s3 = fmaf(colk[i + 96], cj[i + 96], s3);
+          }
+          for (; i < r; i += 32) s0 = fmaf(colk[i], cj[i], s0);
+          float sd = warp_allsum((s0 + s1) + (s2f + s3)) + v0f * cj[k];
+          const float f = tau * sd;
           if (lane == 0) cj[k] -= f * v0f;
-          for (int64_t i = k + 1 + lane; i < r; i += 32) cj[i] = fmaf(-f, colk[i], cj[i]);
+          i = k + 1 + lane;
+          for (; i + 96 < r; i += 128) {
+            const float c0 = cj[i], c1 = cj[i + 32], c2 = cj[i + 64], c3 = cj[i + 96];
+            cj[i] = fmaf(-f, colk[i], c0);
+            cj[i + 32] = fmaf(-f, colk[i + 32], c1);
+            cj[i + 64] = fmaf(-f, colk[i + 64], c2);
+            cj[i + 96] = fmaf(-f, colk[i + 96], c3);
+          }
+          for (; i < r; i += 32) cj[i] = fmaf(-f, colk[i], cj[i]);
         }
       }
       __syncthreads();
@@ -548,6 +762,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
       }
       __syncthreads();
     }
+    phase_mark(3);
     double* beta = sh.dvec[0];
     double* g = sh.dvec[1];
     double* z = sh.dvec[2];
@@ -625,6 +840,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
           break;
         }
     }
+    phase_mark(4);
     // 6. Stage II with the stopping rule confirmed on true gradients
     int total = 0, restarts = 0, converged = 0;
     const double tau = a.tol / 2.0;
@@ -657,6 +873,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
       ++restarts;
     }
     if (status == 0 && !converged) status = 5;
+    phase_mark(5);
     for (int c = tid; c < d; c += blockDim.x) P.beta[c] = beta[c];
     if (tid == 0) {
       *P.status = status;
@@ -688,7 +905,8 @@ struct spcg_batch {
   unsigned char* scratch = nullptr;
   size_t scratch_bytes = 0;
   int grid = 0;
-  int64_t max_rows_int = 0, max_stage_rows = 0, max_r = 0;
+  int64_t max_rows_int = 0, max_stage_rows = 0, max_r = 0, max_n = 0;
+  long long* dphase = nullptr;     // n x 8 phase cycles of the last solve
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t g_seed = 0;
@@ -774,6 +992,7 @@ extern "C" spcg_status spcg_batch_create(const spcg_problem_f32* probs, int32_t 
     b->max_rows_int = std::max(b->max_rows_int, mK + sc.r);
     b->max_stage_rows = std::max(b->max_stage_rows, sum_m);
     b->max_r = std::max(b->max_r, (int64_t)sc.r);
+    b->max_n = std::max(b->max_n, (int64_t)q.N);
     b->host[k] = P;
   }
   b->max_rows_int = (b->max_rows_int + 15) & ~int64_t(15);
@@ -786,11 +1005,14 @@ extern "C" spcg_status spcg_batch_create(const spcg_problem_f32* probs, int32_t 
   b->grid = std::min(sms, n);
   size_t bytes = (size_t)b->max_rows_int * (B_MAXD + 1) * 8 + (size_t)b->max_stage_rows * B_MAXD * 4 +
                  (size_t)b->max_stage_rows * 8 + (size_t)b->max_r * B_MAXD * 4 +
-                 (size_t)3 * B_MAXD * B_MAXD * 4;
+                 (size_t)3 * B_MAXD * B_MAXD * 4 + (size_t)2 * b->max_rows_int * 4 +
+                 (size_t)2 * b->max_n * 4;
   b->scratch_bytes = (bytes + 255) & ~(size_t)255;
   if (cudaMalloc(&b->scratch, b->scratch_bytes * b->grid) != cudaSuccess) return fail(SPCG_E_OOM);
   if (cudaMalloc(&b->dprobs, sizeof(BatchProblemDev) * n) != cudaSuccess) return fail(SPCG_E_OOM);
   if (cudaMalloc(&b->queue, sizeof(int)) != cudaSuccess) return fail(SPCG_E_OOM);
+  if (cudaMalloc(&b->dphase, sizeof(long long) * 8 * n) != cudaSuccess) return fail(SPCG_E_OOM);
+  if (cudaMemset(b->dphase, 0, sizeof(long long) * 8 * n) != cudaSuccess) return fail(SPCG_E_CUDA);
   if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->eu, cudaEventDisableTiming) != cudaSuccess)
     return fail(SPCG_E_CUDA);
@@ -822,6 +1044,7 @@ extern "C" void spcg_batch_destroy(spcg_batch* b) {
   cudaFree(b->dstatus);
   cudaFree(b->diters);
   cudaFree(b->queue);
+  cudaFree(b->dphase);
   cudaFree(b->scratch);
   delete b;
 }
@@ -843,6 +1066,8 @@ static spcg_status batch_capture(spcg_batch* b, uint64_t seed, double tol) {
   a.max_rows_int = b->max_rows_int;
   a.max_stage_rows = b->max_stage_rows;
   a.max_r = b->max_r;
+  a.max_n = b->max_n;
+  a.phase_cycles = b->dphase;
   a.seed = seed;
   a.tol = tol;
   a.max_iters = 100;
@@ -892,6 +1117,25 @@ extern "C" spcg_status spcg_batch_solve(spcg_batch* b, uint64_t seed, double tol
     if (st[k] != 0 && worst == SPCG_OK) worst = (spcg_status)st[k];
   }
   return worst;
+}
+
+extern "C" spcg_status spcg_solve_batched(const spcg_problem_f32* probs, int32_t n, uint64_t seed,
+                                          double tol, void* stream, int32_t* status_out,
+                                          int32_t* iters_out) {
+  spcg_batch* b = nullptr;
+  SPCG_TRY(spcg_batch_create(probs, n, stream, &b));
+  const spcg_status st = spcg_batch_solve(b, seed, tol, status_out, iters_out, nullptr);
+  spcg_batch_destroy(b);
+  return st;
+}
+
+extern "C" spcg_status spcg_batch_phase_cycles(spcg_batch* b, int64_t* cycles_out) {
+  if (!b || !cycles_out) return SPCG_E_INVALID_ARG;
+  std::vector<long long> h((size_t)8 * b->n);
+  SPCG_CK(cudaMemcpy(h.data(), b->dphase, sizeof(long long) * 8 * b->n, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < b->n; ++k)
+    for (int q = 0; q < 8; ++q) cycles_out[(size_t)b->order[k] * 8 + q] = h[(size_t)k * 8 + q];
+  return SPCG_OK;
 }
 
 extern "C" spcg_status spcg_batch_set_tiles(spcg_batch* b, const int32_t* chunk_bytes4) {

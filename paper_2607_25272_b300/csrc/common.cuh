@@ -136,14 +136,16 @@ __device__ __forceinline__ void st_release_gpu_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, int* status, long long spin,
-                                                  int* s_fail) {
+// Barrier of the first `nparts` CTAs of the grid (the others must not call
+// it with the same bar); grid_sync_bounded is the whole grid.
+__device__ __forceinline__ bool group_sync_bounded(unsigned* bar, unsigned nparts, int* status,
+                                                   long long spin, int* s_fail) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned* gen = bar + kBarGen;
     const unsigned g = ld_acquire_gpu_u32(gen);
     const unsigned prev = atom_add_acq_rel_gpu_u32(bar, 1u);
-    if (prev == gridDim.x - 1) {
+    if (prev == nparts - 1) {
       bar[0] = 0u;                      // ordered before the release below
       st_release_gpu_u32(gen, g + 1u);
     } else {
@@ -160,6 +162,11 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, int* status, lo
   }
   __syncthreads();
   return *s_fail == 0;
+}
+
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, int* status, long long spin,
+                                                  int* s_fail) {
+  return group_sync_bounded(bar, gridDim.x, status, spin, s_fail);
 }
 
 }  // namespace spcg

@@ -13,7 +13,8 @@ namespace spcg {
 // Device scalars of one context (one allocation, zeroed at create).
 struct DevScalars {
   int status;        // DEV_* error code, sticky until the next spcg_* call
-  int done;          // stopping test passed (set by the pass prologue / check)
+  int done;          // 0 iterating; 1 the recursive stopping test passed (pass
+                     // prologue); 2 confirmed on a true gradient (k_check)
   int iters;         // PCG iterations that ran a pass since the last reset
   int pad;
   double gam[2];     // gamma ping-pong
@@ -58,7 +59,7 @@ struct PcgBuffers {
   double* dots_gz;   // per precond CTA
   double* dots_rb;
   int n_red;         // CTAs of the reduce kernel
-  int n_pre;         // CTAs of the precond kernels
+  int n_pre;         // (d + 3) / 4: sizes the per-CTA dot arrays
   int n_ds;          // CTAs of k_dspace (= shares in dots_pw, dots_gz, dots_rb)
   int last_grid;     // CTAs of the last fused pass (= partials to reduce)
 };
@@ -94,7 +95,8 @@ struct Sketch {
   double* qr_red = nullptr;     // 2 x SMs x (2 x panel width): per-CTA partial sums
   double* qr_wp = nullptr;      // SMs x panel width x d: per-CTA partials of V^T C
   double* qr_wt = nullptr;      // panel width x d: T^T V^T C
-  unsigned* qr_bar = nullptr;   // grid barrier (kBarWords): arrival count, generation
+  double* qr_tg = nullptr;      // panel width^2: T of the current panel
+  unsigned* qr_bar = nullptr;   // 2 barriers of kBarWords (grid, panel group)
   unsigned long long* colmax = nullptr;  // d + 1: largest |x| per column (bit pattern)
   int* colshift = nullptr;      // d + 1: fixed-point scale exponent per column
   PassGeom geom[SPCG_MAX_STAGES];  // fused-pass geometry of stage i
@@ -191,12 +193,11 @@ spcg_status pass_resid(spcg_ctx* c, const PassGeom& g, const double* b, const do
 spcg_status pass_gram_iter(spcg_ctx* c, const PassGeom& g, int pp, int gp, int start,
                            int check, double tau);
 spcg_status launch_reduce(spcg_ctx* c, double* out, const double* dotvec);
-spcg_status launch_precond_T(spcg_ctx* c, int iter_mode, int cur, int pp, int gp, double* beta);
-spcg_status launch_precond(spcg_ctx* c, int cur, const double* beta);
 spcg_status launch_check(spcg_ctx* c, double tau);
 int dspace_grid(const spcg_ctx* c);
 spcg_status launch_dspace(spcg_ctx* c, int iter, int cur, int pp, int gp, double* beta);
-spcg_status launch_reset_flags(spcg_ctx* c);
+spcg_status launch_reset_flags(spcg_ctx* c);   // also clears the device status
+spcg_status launch_reset_loop(spcg_ctx* c);    // keeps the device status
 spcg_status prof_events(spcg_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1, int op);
 spcg_status prof_collect(spcg_ctx* c);   // after a stream sync
 spcg_status pass_gram_plain(spcg_ctx* c, const PassGeom& g, const double* p);

@@ -6,11 +6,18 @@
 // Sec. 2.2 charges per iteration).  Kernels per iteration:
 //   k_pass      fused prologue (gamma', new p, stopping test) + one read of A:
 //               per-CTA partials of A^T (A p), row tiles staged by TMA
-//   k_reduce    partials -> w (fixed order) and partial dots p.w
-//   k_precondT  alpha, g update, beta update, u = R^{-T} g
-//   k_precond   z = R^{-1} u, partial dots g.z and ||R beta||^2
+//   k_dspace    one cooperative launch: partials -> w and p.w; alpha, g and
+//               beta updates, u = R^{-T} g; z = R^{-1} u and the partial dots
+//               g.z and ||R beta||^2 that the next pass's prologue adds
 // The stage start uses the same pass in residual mode: g = A^T (b - A beta).
+// (k_reduce, the partials -> w sum alone, serves the plain-pass entry points.)
 // All reductions run in a fixed order, so two runs give identical bits.
+//
+// Stopping state (DevScalars::done), kept on the device so that a Stage II
+// schedule can be enqueued without reading it back: 1 when a pass prologue
+// finds the recursive test met (iterations then do nothing), 2 when k_check
+// confirms it on a true gradient (then everything does nothing); k_check sets
+// 0 again when the true gradient fails the test, and iterations resume from it.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -231,7 +238,10 @@ __global__ void __launch_bounds__(PassCfg<NI, sizeof(T)>::THREADS, 1)
   __shared__ double s_scal[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (a.scal->status != 0 || a.scal->done != 0) return;   // uniform over the grid
+  // uniform over the grid: an error, or the stopping test passed (done 1: the
+  // recursive test, only a residual pass still runs, to confirm; done 2:
+  // confirmed on the true gradient)
+  if (a.scal->status != 0 || a.scal->done > (a.mode == PASS_RESID ? 1 : 0)) return;
 
   if (tid == 0) {
     s_flag = 0;
@@ -482,104 +492,6 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ parti
   }
 }
 
-constexpr int kPreWarps = 4;
-
-// u = R^{-T} g_new (RinvT row-major lower); ITER mode first forms
-// alpha = gamma / p.w, g_new = g - alpha w and beta += alpha p.
-__global__ void __launch_bounds__(kPreWarps * 32)
-    k_precondT(int d, int iter_mode, const double* __restrict__ RinvT,
-               const double* __restrict__ g_cur, double* __restrict__ g_nxt,
-               const double* __restrict__ w, const double* __restrict__ p,
-               const double* __restrict__ dots_pw, int n_red, int gp, double* __restrict__ beta,
-               double* __restrict__ u, DevScalars* __restrict__ scal) {
-  if (scal->status != 0 || scal->done != 0) return;
-  extern __shared__ double gs[];
-  __shared__ double s_alpha;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double alpha = 0.0;
-  if (iter_mode) {
-    if (warp == 0) {
-      const double pw = warp_sum_array(dots_pw, n_red);
-      if (lane == 0) {
-        const double al = scal->gam[gp] / pw;
-        s_alpha = (pw > 0.0 && isfinite(al)) ? al : NAN;
-      }
-    }
-    __syncthreads();
-    alpha = s_alpha;
-    if (isnan(alpha)) {
-      if (threadIdx.x == 0) atomicExch(&scal->status, DEV_BREAKDOWN);
-      return;
-    }
-    for (int j = threadIdx.x; j < d; j += blockDim.x) gs[j] = fma(-alpha, w[j], g_cur[j]);
-  } else {
-    for (int j = threadIdx.x; j < d; j += blockDim.x) gs[j] = g_cur[j];
-  }
-  __syncthreads();
-  const int i = blockIdx.x * kPreWarps + warp;
-  if (i >= d) return;
-  const double* Ri = RinvT + (size_t)i * d;
-  double s = 0.0;
-  for (int j = lane; j <= i; j += 32) s = fma(Ri[j], gs[j], s);
-  s = warp_allsum(s);
-  if (lane == 0) {
-    u[i] = s;
-    g_nxt[i] = gs[i];
-    if (iter_mode) beta[i] = fma(alpha, p[i], beta[i]);
-  }
-}
-
-// z = R^{-1} u; per-CTA partial dots g.z and ||R beta||^2.
-__global__ void __launch_bounds__(kPreWarps * 32)
-    k_precond(int d, const double* __restrict__ Rinv, const double* __restrict__ R,
-              const double* __restrict__ u, const double* __restrict__ beta,
-              const double* __restrict__ g, double* __restrict__ z,
-              double* __restrict__ dots_gz, double* __restrict__ dots_rb,
-              const DevScalars* __restrict__ scal) {
-  if (scal->status != 0 || scal->done != 0) return;
-  extern __shared__ double sh[];
-  double* us = sh;
-  double* bs = sh + d;
-  __shared__ double red[2][kPreWarps];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    us[j] = u[j];
-    bs[j] = beta[j];
-  }
-  __syncthreads();
-  const int i = blockIdx.x * kPreWarps + warp;
-  double gz = 0.0, rb2 = 0.0;
-  if (i < d) {
-    const double* Ri = Rinv + (size_t)i * d;
-    const double* Rr = R + (size_t)i * d;
-    double s = 0.0, q = 0.0;
-    for (int j = i + lane; j < d; j += 32) {
-      s = fma(Ri[j], us[j], s);
-      q = fma(Rr[j], bs[j], q);
-    }
-    s = warp_allsum(s);
-    q = warp_allsum(q);
-    if (lane == 0) z[i] = s;
-    gz = g[i] * s;
-    rb2 = q * q;
-  }
-  if (lane == 0) {
-    red[0][warp] = gz;
-    red[1][warp] = rb2;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-#pragma unroll
-    for (int w = 0; w < kPreWarps; ++w) {
-      a += red[0][w];
-      b += red[1][w];
-    }
-    dots_gz[blockIdx.x] = a;
-    dots_rb[blockIdx.x] = b;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // The d-space work between two fused passes in ONE cooperative launch.  It
 // replaces k_reduce + k_precondT + k_precond (three launches) with three
@@ -651,7 +563,9 @@ __global__ void __launch_bounds__(kDsThreads) k_dspace(const DspaceArgs a) {
   __shared__ int s_fail;
   __shared__ double s_red[kDsWarps][2];
   __shared__ double s_alpha;
-  if (a.scal->status != 0 || a.scal->done != 0) return;   // uniform over the grid
+  // uniform over the grid; a (re)start still runs after the recursive test
+  // passed (done 1), to confirm it on the true gradient
+  if (a.scal->status != 0 || a.scal->done > (a.iter ? 0 : 1)) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x, q = blockIdx.x, d = a.d;
   if (tid == 0) s_fail = 0;
@@ -771,10 +685,12 @@ __global__ void __launch_bounds__(kDsThreads) k_dspace(const DspaceArgs a) {
   ds_block_sum2(gz, rb2, s_red, &a.dots_gz[q], &a.dots_rb[q]);
 }
 
-// The stopping test on freshly computed dots (same sums as the pass prologue).
+// The stopping test on freshly computed dots of a true gradient (same sums as
+// the pass prologue): done = 2 (confirmed) when it holds, else 0 (iterate on
+// from this gradient).  Nothing to do once confirmed.
 __global__ void k_check(const double* __restrict__ dots_gz, const double* __restrict__ dots_rb,
                         int n, double tau, DevScalars* __restrict__ scal) {
-  if (scal->status != 0) return;
+  if (scal->status != 0 || scal->done == 2) return;
   const double gam = warp_sum_array(dots_gz, n);
   const double rb2 = warp_sum_array(dots_rb, n);
   if (threadIdx.x == 0) {
@@ -782,7 +698,7 @@ __global__ void k_check(const double* __restrict__ dots_gz, const double* __rest
     scal->sqrt_gamma = sqrt(fmax(gam, 0.0));
     scal->norm_rb = rb;
     if (!isfinite(gam) || gam < 0.0) scal->status = DEV_BREAKDOWN;
-    else scal->done = (gam == 0.0 || sqrt(gam) <= tau * rb) ? 1 : 0;
+    else scal->done = (gam == 0.0 || sqrt(gam) <= tau * rb) ? 2 : 0;
   }
 }
 
@@ -979,28 +895,6 @@ spcg_status launch_reduce(spcg_ctx* c, double* out, const double* dotvec) {
   return SPCG_OK;
 }
 
-spcg_status launch_precond_T(spcg_ctx* c, int iter_mode, int cur, int pp, int gp, double* beta) {
-  const int d = c->d;
-  const int nb = (d + kPreWarps - 1) / kPreWarps;
-  k_precondT<<<nb, kPreWarps * 32, (size_t)d * 8, c->stream>>>(
-      d, iter_mode, c->sk.RinvT, c->pb.g[cur], c->pb.g[cur ^ 1], c->pb.w, c->pb.p[pp],
-      c->pb.dots_pw, (d + 31) / 32, gp, beta, c->pb.u, c->scal);
-  SPCG_CK(cudaGetLastError());
-  c->n_launch += 1;
-  return SPCG_OK;
-}
-
-spcg_status launch_precond(spcg_ctx* c, int cur, const double* beta) {
-  const int d = c->d;
-  const int nb = (d + kPreWarps - 1) / kPreWarps;
-  k_precond<<<nb, kPreWarps * 32, (size_t)2 * d * 8, c->stream>>>(
-      d, c->sk.Rinv, c->sk.R, c->pb.u, beta, c->pb.g[cur], c->pb.z, c->pb.dots_gz,
-      c->pb.dots_rb, c->scal);
-  SPCG_CK(cudaGetLastError());
-  c->n_launch += 1;
-  return SPCG_OK;
-}
-
 // CTAs of k_dspace: about eight columns (and rows) per CTA, at most one per SM.
 int dspace_grid(const spcg_ctx* c) {
   int g = (c->d + 7) / 8;
@@ -1042,6 +936,15 @@ spcg_status launch_dspace(spcg_ctx* c, int iter, int cur, int pp, int gp, double
 
 spcg_status launch_check(spcg_ctx* c, double tau) {
   k_check<<<1, 32, 0, c->stream>>>(c->pb.dots_gz, c->pb.dots_rb, c->pb.n_ds, tau, c->scal);
+  SPCG_CK(cudaGetLastError());
+  c->n_launch += 1;
+  return SPCG_OK;
+}
+
+// Before a loop of passes: clear the stopping flag and the iteration count
+// but keep a device error of earlier work.
+spcg_status launch_reset_loop(spcg_ctx* c) {
+  k_reset<<<1, 1, 0, c->stream>>>(c->scal, 0, c->sk.qr_bar);
   SPCG_CK(cudaGetLastError());
   c->n_launch += 1;
   return SPCG_OK;
@@ -1245,7 +1148,7 @@ __global__ void __launch_bounds__(DfCfg<NI>::THREADS, 1)
   __shared__ int s_abort;
   __shared__ double s_scal[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (a.scal->status != 0 || a.scal->done != 0) return;
+  if (a.scal->status != 0 || a.scal->done > (a.mode == PASS_RESID ? 1 : 0)) return;   // as k_pass
   if (tid == 0) {
     s_abort = 0;
     for (int s = 0; s < a.stages; ++s) {

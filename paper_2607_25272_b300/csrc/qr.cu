@@ -8,15 +8,17 @@
 // Main path, k_qr_coop: blocked Householder QR with the compact WY form
 // (H_0 ... H_{b-1} = I - V T V^T) in ONE cooperative launch, one CTA per SM
 // (fewer for small r), every CTA owning a contiguous block of rows.
-//   Panel of b = 32 columns: each CTA keeps its rows of the panel in shared
-//   memory.  Column step j needs one grid-wide reduction of 2b numbers: the
+//   Panel of b = 32 columns, factored by the first GP CTAs (about 48 rows
+//   each): every panel CTA keeps its rows of the panel in shared memory.
+//   Column step j needs one reduction over the panel CTAs of 2b numbers: the
 //   column's squared norm below the diagonal, its dot products with the
 //   other panel columns below the diagonal, and the panel's values on the
 //   diagonal row.  From these sums every CTA derives alpha, the reflector's
 //   first entry v_0, v^T a_i for the later columns (so each CTA updates its
 //   own rows without a second reduction) and V^T v_j for the column j of T.
-//   Trailing matrix C: W = V^T C (per-CTA partials over its rows), then
-//   W' = T^T W (columns split over CTAs), then C -= V W' (own rows).
+//   Trailing matrix C, on all CTAs (rows of V and T read back from global
+//   memory): W = V^T C (per-CTA partials over its rows), then W' = T^T W
+//   (columns split over CTAs), then C -= V W' (own rows).
 //   A grid barrier separates the phases; its wait is bounded (on expiry the
 //   device status becomes TIMEOUT and every CTA leaves at its next barrier).
 //   Partial sums are added in CTA order, so the result is reproducible.
@@ -191,18 +193,22 @@ constexpr int QT = 256;                // threads per CTA
 constexpr int QLD = QB + 1;            // row stride of the panel slice in shared memory
 constexpr int QCOLB = 8;               // columns per batch in the T^T W phase
 constexpr int QUNR = 8;                // independent loads in flight per thread in the sums
+constexpr int kQrPanelRows = 48;       // rows per panel CTA (default panel group size)
 
 struct QrCoopArgs {
   double* A;           // r x d column-major (ld = r), reduced in place
   int64_t r;
   int d;
-  int chunk_max;       // rows of the largest panel slice of a CTA
+  int gp;              // CTAs that factor the panels (the first gp of the grid)
+  int chunk_max;       // rows of the largest row slice a CTA holds in shared memory
+  double* Tg;          // QB x QB: T of the current panel, for the trailing update
   double* Rdiag;       // d: alpha_k (R_kk before the sign fix)
   double* vdiag;       // d: v_0 of reflector k
   double* red;         // 2 x G x QSL
   double* Wp;          // G x QB x d
   double* Wt;          // QB x d
-  unsigned* bar;       // [0] arrivals, [1] generation (zero at launch)
+  unsigned* bar;       // grid barrier (kBarWords, zero at launch)
+  unsigned* bar2;      // barrier of the panel CTAs (kBarWords, zero at launch)
   int* status;
   long long spin;
 };
@@ -217,6 +223,7 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
   double* wsm = pv0 + QB;                            // QCOLB x QB: W columns of one batch
   __shared__ int s_fail;
   __shared__ double sc[2];   // v_0 and tau of the current reflector
+  __shared__ double fcol[QB];  // tau v^T a_i of the later panel columns
   const int tid = threadIdx.x, G = gridDim.x, q = blockIdx.x;
   if (tid == 0) s_fail = 0;
   if (*a.status != 0) return;                        // uniform: set before this launch
@@ -224,119 +231,135 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
   const int64_t r = a.r;
   const int d = a.d;
   int step = 0;
+  const int GP = a.gp;
   for (int k0 = 0; k0 < d; k0 += QB) {
     const int bw = d - k0 < QB ? d - k0 : QB;
     const int64_t mp = r - k0;
+    if (q < GP) {
+      // ---- panel: the first GP CTAs, each a block of rows in shared memory ----
+      const int64_t chunk = (mp + GP - 1) / GP;
+      const int64_t lo = k0 + (int64_t)q * chunk;
+      const int64_t hi = lo + chunk < r ? lo + chunk : r;
+      const int nr = hi > lo ? (int)(hi - lo) : 0;
+      for (int e = tid; e < nr * QB; e += QT) {
+        const int j = e / nr, ri = e % nr;
+        P[ri * QLD + j] = j < bw ? a.A[(int64_t)(k0 + j) * r + lo + ri] : 0.0;
+      }
+      for (int e = tid; e < QB * QB; e += QT) T[e] = 0.0;
+      __syncthreads();
+      for (int j = 0; j < bw; ++j, ++step) {
+        const int64_t diag = k0 + j;
+        const int own = (diag >= lo && diag < hi) ? (int)(diag - lo) : -1;
+        // slot s < QB: sum over own rows below the diagonal of P[., s] P[., j];
+        // slot QB + s: the diagonal row's value of column s (owner only)
+        {
+          const int sl = tid % QSL, grp = tid / QSL;   // 4 row groups
+          double acc = 0.0;
+          if (sl < QB) {
+            if (sl < bw) {
+              int ri0 = (int)(diag + 1 - lo);
+              if (ri0 < 0) ri0 = 0;
+              for (int ri = ri0 + grp; ri < nr; ri += 4) acc = fma(P[ri * QLD + sl], P[ri * QLD + j], acc);
+            }
+          } else if (grp == 0 && own >= 0 && sl - QB < bw) {
+            acc = P[own * QLD + (sl - QB)];
+          }
+          comb[grp * QSL + sl] = acc;
+        }
+        __syncthreads();
+        double* red = a.red + (size_t)(step & 1) * G * QSL;
+        if (tid < QSL)
+          red[(size_t)q * QSL + tid] =
+              ((comb[tid] + comb[QSL + tid]) + comb[2 * QSL + tid]) + comb[3 * QSL + tid];
+        if (!group_sync_bounded(a.bar2, (unsigned)GP, a.status, a.spin, &s_fail)) return;
+        {
+          // the same sums in every panel CTA: slot sl over CTAs g, g + 4, ...
+          // then the four quarter sums in order
+          const int sl = tid % QSL, grp = tid / QSL;
+          double acc = 0.0;
+          for (int g0 = grp; g0 < GP; g0 += 4 * QUNR) {   // loads first, then the sums in order
+            double v[QUNR];
+#pragma unroll
+            for (int k = 0; k < QUNR; ++k) {
+              const int g = g0 + 4 * k;
+              v[k] = g < GP ? red[(size_t)g * QSL + sl] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < QUNR; ++k) acc += v[k];
+          }
+          comb[grp * QSL + sl] = acc;
+        }
+        __syncthreads();
+        if (tid < QSL) tot[tid] = ((comb[tid] + comb[QSL + tid]) + comb[2 * QSL + tid]) + comb[3 * QSL + tid];
+        __syncthreads();
+        if (tid == 0) {   // the reflector's scalars, once per CTA (FP64 sqrt and divide are slow)
+          const double s2 = tot[j], x0 = tot[QB + j];
+          const double normx = sqrt(fma(x0, x0, s2));
+          const double alpha = (x0 >= 0.0) ? -normx : normx;
+          const double v0 = x0 - alpha;
+          const double vv = fma(v0, v0, s2);
+          pv0[j] = v0;
+          sc[0] = v0;
+          sc[1] = vv > 0.0 ? 2.0 / vv : 0.0;
+          if (q == 0) {
+            a.Rdiag[diag] = alpha;
+            a.vdiag[diag] = v0;
+          }
+        }
+        __syncthreads();
+        const double v0 = sc[0], tau = sc[1];
+        // T(0:j, j) = -tau T(0:j, 0:j) V(:, 0:j)^T v_j, with
+        // v_l^T v_j = (below the diagonal) + v_l(diag) v_0
+        if (tid < j) {
+          double sacc = 0.0;
+          for (int l = tid; l < j; ++l) sacc = fma(T[tid * QB + l], fma(tot[QB + l], v0, tot[l]), sacc);
+          T[tid * QB + j] = -tau * sacc;
+        } else if (tid == j) {
+          T[j * QB + j] = tau;
+        }
+        // later panel columns, own rows: a_i -= f_i v with f_i = tau (v^T a_i),
+        // formed once per column (FP64 operations are the scarce resource here)
+        const int ncl = bw - j - 1;
+        if (tid > j && tid < bw) fcol[tid] = tau * fma(v0, tot[QB + tid], tot[tid]);
+        __syncthreads();
+        for (int e = tid; e < nr * ncl; e += QT) {
+          const int i = j + 1 + e / nr, ri = e % nr;
+          const int64_t row = lo + ri;
+          if (row < diag) continue;
+          const double vr = (row == diag) ? v0 : P[ri * QLD + j];
+          P[ri * QLD + i] = fma(-fcol[i], vr, P[ri * QLD + i]);
+        }
+        __syncthreads();
+      }
+      // write the panel back (R above the diagonal, v below it, x_0 on it);
+      // the panel's T goes to global memory for the trailing update
+      for (int e = tid; e < nr * bw; e += QT) {
+        const int j = e / nr, ri = e % nr;
+        a.A[(int64_t)(k0 + j) * r + lo + ri] = P[ri * QLD + j];
+      }
+      if (q == 0)
+        for (int e = tid; e < QB * QB; e += QT) a.Tg[e] = T[e];
+    } else {
+      step += bw;   // keep the reduction buffers' parity in step with the panel CTAs
+    }
+    const int nt = d - k0 - bw;   // trailing columns
+    if (nt <= 0) break;           // last panel: nothing to update
+    if (!grid_sync_bounded(a.bar, a.status, a.spin, &s_fail)) return;
+    // ---- trailing update on all CTAs: this CTA's rows of V (0 above the
+    // diagonal, v_0 on it) and T from global memory ----
     const int64_t chunk = (mp + G - 1) / G;
     const int64_t lo = k0 + (int64_t)q * chunk;
     const int64_t hi = lo + chunk < r ? lo + chunk : r;
     const int nr = hi > lo ? (int)(hi - lo) : 0;
-    // this CTA's rows of the panel (coalesced along each column)
     for (int e = tid; e < nr * QB; e += QT) {
-      const int j = e / nr, ri = e % nr;
-      P[ri * QLD + j] = j < bw ? a.A[(int64_t)(k0 + j) * r + lo + ri] : 0.0;
-    }
-    for (int e = tid; e < QB * QB; e += QT) T[e] = 0.0;
-    __syncthreads();
-    for (int j = 0; j < bw; ++j, ++step) {
-      const int64_t diag = k0 + j;
-      const int own = (diag >= lo && diag < hi) ? (int)(diag - lo) : -1;
-      // slot s < QB: sum over own rows below the diagonal of P[., s] P[., j];
-      // slot QB + s: the diagonal row's value of column s (owner only)
-      {
-        const int sl = tid % QSL, grp = tid / QSL;   // 4 row groups
-        double acc = 0.0;
-        if (sl < QB) {
-          if (sl < bw) {
-            int ri0 = (int)(diag + 1 - lo);
-            if (ri0 < 0) ri0 = 0;
-            for (int ri = ri0 + grp; ri < nr; ri += 4) acc = fma(P[ri * QLD + sl], P[ri * QLD + j], acc);
-          }
-        } else if (grp == 0 && own >= 0 && sl - QB < bw) {
-          acc = P[own * QLD + (sl - QB)];
-        }
-        comb[grp * QSL + sl] = acc;
-      }
-      __syncthreads();
-      double* red = a.red + (size_t)(step & 1) * G * QSL;
-      if (tid < QSL)
-        red[(size_t)q * QSL + tid] =
-            ((comb[tid] + comb[QSL + tid]) + comb[2 * QSL + tid]) + comb[3 * QSL + tid];
-      if (!grid_sync_bounded(a.bar, a.status, a.spin, &s_fail)) return;
-      {
-        // the same sums in every CTA: slot sl over CTAs g, g + 4, ... then the
-        // four quarter sums in order
-        const int sl = tid % QSL, grp = tid / QSL;
-        double acc = 0.0;
-        for (int g0 = grp; g0 < G; g0 += 4 * QUNR) {   // loads first, then the sums in order
-          double v[QUNR];
-#pragma unroll
-          for (int k = 0; k < QUNR; ++k) {
-            const int g = g0 + 4 * k;
-            v[k] = g < G ? red[(size_t)g * QSL + sl] : 0.0;
-          }
-#pragma unroll
-          for (int k = 0; k < QUNR; ++k) acc += v[k];
-        }
-        comb[grp * QSL + sl] = acc;
-      }
-      __syncthreads();
-      if (tid < QSL) tot[tid] = ((comb[tid] + comb[QSL + tid]) + comb[2 * QSL + tid]) + comb[3 * QSL + tid];
-      __syncthreads();
-      if (tid == 0) {   // the reflector's scalars, once per CTA (FP64 sqrt and divide are slow)
-        const double s2 = tot[j], x0 = tot[QB + j];
-        const double normx = sqrt(fma(x0, x0, s2));
-        const double alpha = (x0 >= 0.0) ? -normx : normx;
-        const double v0 = x0 - alpha;
-        const double vv = fma(v0, v0, s2);
-        pv0[j] = v0;
-        sc[0] = v0;
-        sc[1] = vv > 0.0 ? 2.0 / vv : 0.0;
-        if (q == 0) {
-          a.Rdiag[diag] = alpha;
-          a.vdiag[diag] = v0;
-        }
-      }
-      __syncthreads();
-      const double v0 = sc[0], tau = sc[1];
-      // T(0:j, j) = -tau T(0:j, 0:j) V(:, 0:j)^T v_j, with
-      // v_l^T v_j = (below the diagonal) + v_l(diag) v_0
-      if (tid < j) {
-        double sacc = 0.0;
-        for (int l = tid; l < j; ++l) sacc = fma(T[tid * QB + l], fma(tot[QB + l], v0, tot[l]), sacc);
-        T[tid * QB + j] = -tau * sacc;
-      } else if (tid == j) {
-        T[j * QB + j] = tau;
-      }
-      // later panel columns, own rows: a_i -= tau (v^T a_i) v
-      const int ncl = bw - j - 1;
-      for (int e = tid; e < nr * ncl; e += QT) {
-        const int i = j + 1 + e / nr, ri = e % nr;
-        const int64_t row = lo + ri;
-        if (row < diag) continue;
-        const double f = tau * fma(v0, tot[QB + i], tot[i]);
-        const double vr = (row == diag) ? v0 : P[ri * QLD + j];
-        P[ri * QLD + i] = fma(-f, vr, P[ri * QLD + i]);
-      }
-      __syncthreads();
-    }
-    // write the panel back (R above the diagonal, v below it, x_0 on it)
-    for (int e = tid; e < nr * bw; e += QT) {
-      const int j = e / nr, ri = e % nr;
-      a.A[(int64_t)(k0 + j) * r + lo + ri] = P[ri * QLD + j];
-    }
-    __syncthreads();
-    // the CTA's rows of V: v_i(row) = 0 above the diagonal, v_0 on it
-    for (int e = tid; e < nr * QB; e += QT) {
-      const int ri = e / QB, i = e % QB;
+      const int i = e / nr, ri = e % nr;
       const int64_t row = lo + ri;
       double v = 0.0;
-      if (i < bw) v = row > k0 + i ? P[ri * QLD + i] : (row == k0 + i ? pv0[i] : 0.0);
+      if (i < bw) v = row > k0 + i ? a.A[(int64_t)(k0 + i) * r + row] : (row == k0 + i ? a.vdiag[k0 + i] : 0.0);
       P[ri * QLD + i] = v;
     }
+    for (int e = tid; e < QB * QB; e += QT) T[e] = a.Tg[e];
     __syncthreads();
-    const int nt = d - k0 - bw;   // trailing columns
-    if (nt <= 0) break;           // last panel: nothing to update
     // W partial = V_own^T C_own
     for (int c = tid; c < nt; c += QT) {
       double w[QB];
@@ -488,10 +511,10 @@ __global__ void k_transpose(const double* __restrict__ S, int d, double* __restr
   }
 }
 
-// Rows of the first (largest) panel slice per CTA and the grid of the
-// cooperative QR: at least about 24 rows per CTA, at most one CTA per SM.
+// The grid of the cooperative QR: at least about 8 rows per CTA, at most one
+// CTA per SM (the trailing updates are FP64-bound: every SM helps).
 static int qr_coop_grid(int64_t r, int sms) {
-  int64_t g = (r + 23) / 24;
+  int64_t g = (r + 7) / 8;
   if (g > sms) g = sms;
   if (g < 1) g = 1;
   return (int)g;
@@ -544,7 +567,14 @@ spcg_status launch_precond_factor(spcg_ctx* c) {
   const int d = c->d;
   const int64_t r = s.sched.r;
   int G = qr_coop_grid(r, c->num_sms);
-  const int64_t chunk_max = (r + G - 1) / G;
+  // the panels are factored by the first GP CTAs, about kQrPanelRows rows each:
+  // fewer CTAs in each column step's reduction and barrier (latency), more rows
+  // each (the step's FP64 work); the trailing updates use all G CTAs
+  int GP = c->opts.qr_panel_ctas > 0 ? c->opts.qr_panel_ctas
+                                     : (int)((r + kQrPanelRows - 1) / kQrPanelRows);
+  if (GP > G) GP = G;
+  if (GP < 1) GP = 1;
+  const int64_t chunk_max = (r + GP - 1) / GP;
   const size_t smem = qr_coop_smem(chunk_max);
   bool coop = smem <= (size_t)200 * 1024 && c->opts.qr_by_column == 0;
   if (coop) {
@@ -554,12 +584,15 @@ spcg_status launch_precond_factor(spcg_ctx* c) {
     if (per_sm < 1) coop = false;   // cannot be co-resident: use the per-column steps
   }
   if (coop) {
-    SPCG_CK(cudaMemsetAsync(s.qr_bar, 0, kBarWords * sizeof(unsigned), c->stream));
+    SPCG_CK(cudaMemsetAsync(s.qr_bar, 0, 2 * kBarWords * sizeof(unsigned), c->stream));
     QrCoopArgs a{};
     a.A = s.Ahat;
     a.r = r;
     a.d = d;
+    a.gp = GP;
     a.chunk_max = (int)chunk_max;
+    a.Tg = s.qr_tg;
+    a.bar2 = s.qr_bar + kBarWords;
     a.Rdiag = s.Rdiag;
     a.vdiag = s.qr_vdiag;
     a.red = s.qr_red;

@@ -90,7 +90,7 @@ class Opts(ctypes.Structure):
         ("qr_by_column", ctypes.c_int32),
         ("fwht_tile", ctypes.c_int32),
         ("fwht_first_levels", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("qr_panel_ctas", ctypes.c_int32),
     ]
 
 
@@ -167,6 +167,11 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_double)]),
     "spcg_batch_set_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "spcg_batch_phase_cycles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "spcg_solve_batched": (ctypes.c_int, [ctypes.POINTER(ProblemF32), ctypes.c_int32,
+                                          ctypes.c_uint64, ctypes.c_double, _P,
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]),
     "spcg_batch_autotune": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_int32)]),
     "spcg_num_candidates": (ctypes.c_int32, []),
@@ -190,6 +195,8 @@ _SIGS = {
     "spcg_probe_fma_tflops": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_double), _P]),
     "spcg_host_pool_trim": (ctypes.c_int, []),
+    "spcg_solve_enqueue": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32]),
+    "spcg_solve_result": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "spcg_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                        ctypes.c_uint64, ctypes.POINTER(Schedule),
                                        ctypes.POINTER(Opts), _P, _P, ctypes.POINTER(Info)]),
@@ -348,6 +355,19 @@ class Solver:
         if raise_on_error:
             _check(st, "spcg_solve")
         return beta, info, st
+
+    def solve_enqueue(self, beta, rounds=6, iters_per_round=20):
+        """Enqueue the stages and a fixed Stage II schedule without any host
+        read (capture-safe; needs a prior sketch)."""
+        _check(lib().spcg_solve_enqueue(self.ctx, _ptr(beta), rounds, iters_per_round),
+               "spcg_solve_enqueue")
+
+    def solve_result(self, raise_on_error=True):
+        info = Info()
+        st = lib().spcg_solve_result(self.ctx, ctypes.byref(info))
+        if raise_on_error:
+            _check(st, "spcg_solve_result")
+        return info, st
 
     def features(self, beta):
         out = (ctypes.c_float * 4)()
@@ -573,6 +593,25 @@ def spcg_host_pool_trim():
     _check(lib().spcg_host_pool_trim(), "spcg_host_pool_trim")
 
 
+def spcg_solve_batched(Xs, Ys, seed, tol=1e-6, stream=None):
+    """Solve a batch in one call (create, solve, destroy).  Returns
+    (betas, statuses, Stage II iterations, first non-zero status)."""
+    import torch
+    n = len(Xs)
+    betas = [torch.zeros(X.shape[1], dtype=torch.float64, device=X.device) for X in Xs]
+    arr = (ProblemF32 * n)()
+    for i, (X, Y, b) in enumerate(zip(Xs, Ys, betas)):
+        if X.dtype != torch.float32 or Y.dtype != torch.float32 or X.stride(1) != 1:
+            raise ValueError("batched problems take row-major float32 X and float32 Y")
+        arr[i].X, arr[i].Y = X.data_ptr(), Y.data_ptr()
+        arr[i].N, arr[i].d, arr[i].ldx = X.shape[0], X.shape[1], X.stride(0)
+        arr[i].beta = b.data_ptr()
+    st = (ctypes.c_int32 * n)()
+    it = (ctypes.c_int32 * n)()
+    rc = lib().spcg_solve_batched(arr, n, seed, tol, _stream_ptr(stream), st, it)
+    return betas, list(st), list(it), rc
+
+
 class Batch:
     """Owner of an spcg_batch over lists of FP32 CUDA tensors X_i (N_i x d_i), Y_i."""
 
@@ -610,6 +649,13 @@ class Batch:
         ch = (ctypes.c_int32 * 4)()
         _check(lib().spcg_batch_autotune(self.h, seed, tol, ch), "spcg_batch_autotune")
         return list(ch)
+
+    def phase_cycles(self):
+        """Per problem, the SM clock cycles of each phase of the last solve
+        (column maxima, CountSketch, stage matrices, QR, Stage I, Stage II)."""
+        arr = (ctypes.c_int64 * (8 * self.n))()
+        _check(lib().spcg_batch_phase_cycles(self.h, arr), "spcg_batch_phase_cycles")
+        return [list(arr[8 * i: 8 * i + 6]) for i in range(self.n)]
 
     def set_tiles(self, chunk_bytes4):
         arr = (ctypes.c_int32 * 4)(*chunk_bytes4)

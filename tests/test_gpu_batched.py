@@ -101,3 +101,14 @@ def test_batched_every_row_width():
         X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
         assert rel_pred_error(X64, beta.cpu().numpy(), ols(X64, Y64)) <= 1e-6, X.shape
     B.close()
+
+
+def test_one_call_batched_solve():
+    """spcg_solve_batched: create, solve and destroy in one call, same answers."""
+    probs = make_batch(6, seed=31)
+    Xs, Ys = to_device(probs)
+    betas, st, it, rc = S.spcg_solve_batched(Xs, Ys, 5, 1e-6)
+    assert rc == S.SPCG_OK and all(v == 0 for v in st)
+    for (X, Y), beta in zip(probs, betas):
+        X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+        assert rel_pred_error(X64, beta.cpu().numpy(), ols(X64, Y64)) <= 1e-6

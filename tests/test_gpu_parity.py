@@ -208,7 +208,8 @@ def test_transform_variants_and_plans_are_bit_identical():
 
 # Both factorisations of the preconditioner sketch: the blocked cooperative QR
 # (panels of 32 columns; widths below, at and just above one panel, ragged
-# last panels) and the per-column steps, each against the oracle's R within
+# last panels; panel groups of the default size, one CTA and five CTAs) and
+# the per-column steps, each against the oracle's R within
 # the Householder backward-error bound; a sketch of 120000 rows takes the
 # per-column path either way (its panel rows do not fit in shared memory).
 @pytest.mark.parametrize("N,d,r,seed", [(20000, 50, None, 1), (4000, 32, None, 2), (4000, 33, None, 3),
@@ -226,9 +227,11 @@ def test_qr_blocked_and_per_column_agree(N, d, r, seed):
     kappa = np.linalg.cond(A_hat)
     tol_R = 2 * math.sqrt(2) * kappa * gamma(r * d) * (np.linalg.norm(A_hat) / np.linalg.norm(A_hat, 2))
     Rs = []
-    for by_col in (0, 1):
+    # blocked QR (automatic panel group, one panel CTA, five), then per column
+    for by_col, panel_ctas in ((0, 0), (0, 1), (0, 5), (1, 0)):
         o = S.Opts()
         o.qr_by_column = by_col
+        o.qr_panel_ctas = panel_ctas
         s = S.Solver(cuda(X), cuda(Y), o)
         sc = S.spcg_default_schedule(N, d)
         sc.r = r
@@ -240,7 +243,8 @@ def test_qr_blocked_and_per_column_agree(N, d, r, seed):
         assert np.array_equal(Rinv_g, np.triu(Rinv_g))
         assert np.linalg.norm(R_g @ Rinv_g - np.eye(d)) <= 4 * d * U * np.linalg.cond(R_g) * math.sqrt(d)
         Rs.append(R_g)
-    assert np.linalg.norm(Rs[0] - Rs[1]) <= 2 * tol_R * np.linalg.norm(R_o, 2)
+    for R_g in Rs[1:]:
+        assert np.linalg.norm(Rs[0] - R_g) <= 2 * tol_R * np.linalg.norm(R_o, 2)
 
 
 # ---------------------------------------------------------------- stages ----
@@ -317,6 +321,40 @@ def test_solve_is_deterministic():
     b1 = b1.clone()
     b2, _, _ = s.solve(4)
     assert torch.equal(b1, b2)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [S.PREC_FP64, S.PREC_MIXED])
+def test_capture_safe_solve_replays_as_a_cuda_graph(prec):
+    """spcg_solve_enqueue launches the stages and a fixed Stage II schedule with
+    no host read, so the sequence can be captured into a CUDA graph: the
+    replayed graph meets the target against the oracle's OLS estimator, bit
+    for bit like the same sequence run uncaptured."""
+    N, d, seed = 40000, 64, 11
+    X, Y, _ = svd_problem(N, d, 1e4, 0.2, seed=seed)
+    bh = OL.ols(X, Y)
+    cs = torch.cuda.Stream()
+    o = S.Opts()
+    o.precision = prec
+    s = S.Solver(cuda(X), cuda(Y), o, stream=cs)
+    s.sketch(4, S.spcg_default_schedule(N, d))          # synchronises: outside the capture
+    beta = torch.zeros(d, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(cs):
+        s.solve_enqueue(beta, rounds=6, iters_per_round=20)
+        info, st = s.solve_result()
+    assert st == S.SPCG_OK and info.converged == 1
+    assert rel_pred_error(X, beta.cpu().numpy(), bh) <= 1e-6
+    b_direct = beta.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cs):
+        s.solve_enqueue(beta, rounds=6, iters_per_round=20)
+    for _ in range(2):
+        with torch.cuda.stream(cs):        # the context's stream: solve_result syncs it
+            beta.fill_(float("nan"))
+            g.replay()
+        info, st = s.solve_result()
+        assert st == S.SPCG_OK and info.converged == 1
+        assert torch.equal(beta, b_direct)
     s.close()
 
 
