@@ -591,7 +591,7 @@ def run_pass_only(args, w, local_rank):
     dev = torch.device("cuda", local_rank)
     g = torch.Generator(device=dev)
     g.manual_seed(1)
-    m, d = args.rows, w["d"]
+    m, d = args.rows, (args.cols or w["d"])
     pair = args.pass_dtype == "pair"
     dt = torch.float32 if pair else getattr(torch, args.pass_dtype)
     align = 16 // torch.empty(0, dtype=dt).element_size()     # rows 16-byte aligned (TMA)
@@ -648,7 +648,7 @@ def run_sketch_only(args, w, local_rank):
     dev = torch.device("cuda", local_rank)
     g = torch.Generator(device=dev)
     g.manual_seed(1)
-    m, d = args.rows, w["d"]
+    m, d = args.rows, (args.cols or w["d"])
     X = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g)
     Y = torch.randn(m, dtype=torch.float64, device=dev, generator=g)
     o = S.Opts()
@@ -686,14 +686,17 @@ def run_solve_only(args, w, local_rank):
     dev = torch.device("cuda", local_rank)
     g = torch.Generator(device=dev)
     g.manual_seed(1)
-    m, d = args.rows, w["d"]
+    m, d = args.rows, (args.cols or w["d"])
     X = torch.randn((m, d), dtype=torch.float64, device=dev, generator=g)
     Y = torch.randn(m, dtype=torch.float64, device=dev, generator=g)
-    s = S.Solver(X, Y)
+    o = S.Opts()
+    o.dspace_ctas = args.dspace_ctas
+    s = S.Solver(X, Y, o)
     stream = torch.cuda.current_stream(dev)
     ms, outs = time_solves(s, 1, None, args.steps, args.warmup, stream)
     _, info, st = outs[-1]
     print(json.dumps({"kernel": "spcg_solve", "rows": m, "d": d, "ms_per_call": ms,
+                      "dspace_ctas": args.dspace_ctas,
                       "status": S.STATUS[st], "launches": info.launches,
                       "refine_iters": info.refine_iters}), flush=True)
     s.close()
@@ -933,6 +936,8 @@ def main():
     ap.add_argument("--kernel", default=None, choices=[None, "pass", "sketch", "solve", "batched"],
                     help="time one kernel alone instead of the solve")
     ap.add_argument("--rows", type=int, default=1 << 18)
+    ap.add_argument("--cols", type=int, default=0,
+                    help="columns for --kernel pass|sketch|solve (0: the workload's d)")
     ap.add_argument("--batch", type=int, default=32, help="problems for --kernel batched")
     ap.add_argument("--weights", default=None, help="schedule model weights (npz) for c5")
     ap.add_argument("--ncu-region", default=None, choices=[None, "plain", "mixed"],
@@ -946,6 +951,8 @@ def main():
                     help="spcg_opts.qr_by_column for --kernel sketch")
     ap.add_argument("--qr-panel-ctas", type=int, default=0,
                     help="spcg_opts.qr_panel_ctas for --kernel sketch")
+    ap.add_argument("--dspace-ctas", type=int, default=0,
+                    help="spcg_opts.dspace_ctas for --kernel solve")
     ap.add_argument("--pass-dtype", default="float64",
                     choices=["float64", "float32", "bfloat16", "pair"])
     args = ap.parse_args()

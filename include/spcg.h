@@ -139,6 +139,10 @@ typedef struct {
   int32_t qr_panel_ctas;    /* CTAs that factor each 32-column panel of the
                                preconditioner QR; 0 = about one per 48 rows of
                                the sketch (at most one per SM)                 */
+  int32_t dspace_ctas;      /* CTAs of the per-iteration d-space step (alpha,
+                               g, beta, z = R^{-1} R^{-T} g and its dots, one
+                               cooperative launch); 0 = about one per 8
+                               columns; at most one per SM and one per column */
 } spcg_opts;
 
 /* Stage II operand of the mixed path (spcg_opts.inner_prec, spcg_info.inner_prec).

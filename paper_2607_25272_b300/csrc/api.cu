@@ -3,6 +3,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -455,10 +456,10 @@ static spcg_status create_impl(const double* X, const double* Y, int64_t N, int3
     if ((st = dalloc(c, v, (size_t)d)) != SPCG_OK) return fail(st);
     if (cudaMemsetAsync(*v, 0, (size_t)d * 8, c->stream) != cudaSuccess) return fail(SPCG_E_CUDA);
   }
-  if ((st = dalloc(c, &pb.dots_pw, (size_t)(pb.n_pre > pb.n_red ? pb.n_pre : pb.n_red))) != SPCG_OK)
-    return fail(st);
-  if ((st = dalloc(c, &pb.dots_gz, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
-  if ((st = dalloc(c, &pb.dots_rb, (size_t)pb.n_pre)) != SPCG_OK) return fail(st);
+  const int n_dots = std::max(std::max(pb.n_pre, pb.n_red), pb.n_ds);
+  if ((st = dalloc(c, &pb.dots_pw, (size_t)n_dots)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &pb.dots_gz, (size_t)n_dots)) != SPCG_OK) return fail(st);
+  if ((st = dalloc(c, &pb.dots_rb, (size_t)n_dots)) != SPCG_OK) return fail(st);
   Sketch& s = c->sk;
   if ((st = dalloc(c, &s.Rdiag, (size_t)d)) != SPCG_OK) return fail(st);
   if ((st = dalloc(c, &s.R, (size_t)d * d)) != SPCG_OK) return fail(st);
@@ -475,7 +476,7 @@ static spcg_status create_impl(const double* X, const double* Y, int64_t N, int3
     return fail(SPCG_E_INVALID_ARG);
   if (c->opts.fwht_tile < 0 || c->opts.fwht_tile > 3 || c->opts.fwht_first_levels < 0 ||
       c->opts.fwht_first_levels > 12 || c->opts.max_workspace_bytes < 0 ||
-      c->opts.qr_panel_ctas < 0)
+      c->opts.qr_panel_ctas < 0 || c->opts.dspace_ctas < 0)
     return fail(SPCG_E_INVALID_ARG);
   if (c->opts.precision == SPCG_PREC_MIXED) {
     c->ldxf = (d + 3) & ~int64_t(3);
@@ -654,14 +655,23 @@ extern "C" spcg_status spcg_refine(spcg_ctx* c, double tol, int32_t max_iters, d
   return st;
 }
 
+// The sketch of a solve; in the mixed form the FP32 split of X runs first and
+// hands the sketch its column maxima (one read of X fewer).
+static spcg_status sketch_after_split(spcg_ctx* c, uint64_t seed, const spcg_schedule* sched) {
+  if (c->opts.precision != SPCG_PREC_MIXED) return spcg_sketch(c, seed, sched);
+  SPCG_TRY(launch_to_f32_colmax(c));
+  const spcg_status st = spcg_sketch(c, seed, sched);
+  c->sk.colmax_pre = false;   // only that sketch may use them
+  return st;
+}
+
 extern "C" spcg_status spcg_solve(spcg_ctx* c, uint64_t seed, const spcg_schedule* sched,
                                   double* beta, spcg_info* info) {
   if (!c || !beta) return SPCG_E_INVALID_ARG;
   if (info) memset(info, 0, sizeof(*info));
   reset_accounting(c);
   SPCG_CK(cudaEventRecord(c->ev[0], c->stream));
-  SPCG_TRY(spcg_sketch(c, seed, sched));
-  if (c->opts.precision == SPCG_PREC_MIXED) SPCG_TRY(launch_to_f32(c));
+  SPCG_TRY(sketch_after_split(c, seed, sched));
   SPCG_CK(cudaEventRecord(c->ev[1], c->stream));
   const spcg_schedule& sc = c->sk.sched;
   SPCG_CK(cudaMemsetAsync(c->beta_work, 0, (size_t)c->d * 8, c->stream));
@@ -1004,8 +1014,7 @@ static spcg_status solve_choice(spcg_ctx* c, uint64_t seed, const uint16_t* Wb, 
                     c->sk.sched.sketch == SPCG_SKETCH_SRHT && c->sk.sched.K == sc.K &&
                     (sc.K == 0 || c->sk.sched.m[sc.K - 1] == sc.m[sc.K - 1]);
   if (!have) {
-    SPCG_TRY(spcg_sketch(c, seed, &sc));   // the prefix holds N'/2 rows: every candidate fits
-    if (c->opts.precision == SPCG_PREC_MIXED) SPCG_TRY(launch_to_f32(c));
+    SPCG_TRY(sketch_after_split(c, seed, &sc));   // the prefix holds N'/2 rows: every candidate fits
   }
   SPCG_CK(cudaEventRecord(c->ev[1], c->stream));
   SPCG_CK(cudaMemsetAsync(c->beta_work, 0, (size_t)c->d * 8, c->stream));

@@ -486,7 +486,7 @@ static spcg_status launch_logl(int logl, const FwhtArgs& a, int64_t nbases, cuda
     if (logl == 9) return launch_tile<9, 2>(a, nbases, st);
     if (logl == 10) return launch_tile<10, 2>(a, nbases, st);
   }
-  if (variant >= 1) {
+  if (variant == 1 || variant == 2) {
     switch (logl) {
       case 9: return launch_tile<9, 1>(a, nbases, st);
       case 10: return launch_tile<10, 1>(a, nbases, st);
@@ -511,7 +511,6 @@ static spcg_status launch_logl(int logl, const FwhtArgs& a, int64_t nbases, cuda
   }
 }
 
-// Split n index bits into passes of at most 12 bits, as even as possible.
 // Split n index bits into passes of at most 12 bits, as even as possible,
 // the larger passes first; first_levels (> 0) fixes the first pass of a
 // two-pass plan instead.
@@ -530,16 +529,20 @@ int fwht_pass_plan(int n, int* logl, int first_levels) {
 spcg_status launch_colscales(spcg_ctx* c) {
   Sketch& s = c->sk;
   const int C = c->d + 1;
-  SPCG_CK(cudaMemsetAsync(s.colmax, 0, (size_t)C * sizeof(unsigned long long), c->stream));
-  int cg = (int)((c->N + 63) / 64);
-  if (cg > 8 * c->num_sms) cg = 8 * c->num_sms;
-  if (cg < 1) cg = 1;
-  k_colmax<<<cg, 256, 0, c->stream>>>(c->X, c->ldx, c->Y, c->N, c->d, s.colmax);
-  SPCG_CK(cudaGetLastError());
+  if (!s.colmax_pre) {
+    SPCG_CK(cudaMemsetAsync(s.colmax, 0, (size_t)C * sizeof(unsigned long long), c->stream));
+    int cg = (int)((c->N + 63) / 64);
+    if (cg > 8 * c->num_sms) cg = 8 * c->num_sms;
+    if (cg < 1) cg = 1;
+    k_colmax<<<cg, 256, 0, c->stream>>>(c->X, c->ldx, c->Y, c->N, c->d, s.colmax);
+    SPCG_CK(cudaGetLastError());
+    c->n_launch += 1;
+  }
+  s.colmax_pre = false;
   k_colscale<<<(C + 255) / 256, 256, 0, c->stream>>>(s.colmax, C, s.nbits, s.colshift,
                                                  &c->scal->status);
   SPCG_CK(cudaGetLastError());
-  c->n_launch += 2;
+  c->n_launch += 1;
   return SPCG_OK;
 }
 
@@ -652,56 +655,113 @@ __device__ __forceinline__ void split_f32(double x, float& h, float& l) {
 }
 
 // Xh, Xl for an N x d block: one warp per row, 16-byte loads, four loads in
-// flight per lane before the stores.
+// flight per lane before the stores.  With CM, the same read of X also yields
+// per-column maxima for the fixed-point scales: the largest high word (sign
+// cleared) of the IEEE patterns of each column of X and of Y.  The high word
+// holds the exponent, and k_colscale reads only the exponent, so the scales
+// equal those from k_colmax's full maxima.  A lane keeps the maxima of its
+// fixed column pairs in registers, a CTA merges them in shared memory and
+// posts one atomicMax per column (as high word << 32).
+template <bool CM>
 __global__ void __launch_bounds__(256) k_to_f32(const double* __restrict__ X, int64_t ldx,
                                                 int64_t N, int d, float* __restrict__ Xf,
-                                                float* __restrict__ Xl, int64_t ldxf) {
+                                                float* __restrict__ Xl, int64_t ldxf,
+                                                const double* __restrict__ Y,
+                                                unsigned long long* __restrict__ colmax) {
   constexpr int U = 4;
+  constexpr int S = (SPCG_MAX_D / 2 + 32 * U - 1) / (32 * U);   // column-pair steps
+  __shared__ unsigned smax[CM ? SPCG_MAX_D + 1 : 1];
   const int lane = threadIdx.x & 31;
   const int full = d / 2;   // complete column pairs
+  unsigned mx[S][U][2], mtail = 0, my = 0;
+  if (CM) {
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int u = 0; u < U; ++u) mx[s][u][0] = mx[s][u][1] = 0;
+    for (int c = threadIdx.x; c <= d; c += blockDim.x) smax[c] = 0;
+  }
   for (int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); i < N;
        i += (int64_t)gridDim.x * 8) {
     const double* xr = X + i * ldx;
     float* hr = Xf + i * ldxf;
     float* lr = Xl + i * ldxf;
-    for (int q0 = 0; q0 < full; q0 += 32 * U) {
-      double2 v[U];
+    // one block of S steps covers d <= SPCG_MAX_D (the CM case); the plain
+    // split takes any d
+    for (int qb = 0; qb < full; qb += S * 32 * U)
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int q = q0 + u * 32 + lane;
-        if (q < full) v[u] = __ldcs(reinterpret_cast<const double2*>(xr) + q);
-      }
+    for (int s = 0; s < S; ++s) {
+      const int q0 = qb + s * 32 * U;
+      if (q0 < full) {
+        double2 v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int q = q0 + u * 32 + lane;
-        if (q < full) {
-          float h0, l0, h1, l1;
-          split_f32(v[u].x, h0, l0);
-          split_f32(v[u].y, h1, l1);
-          reinterpret_cast<float2*>(hr)[q] = make_float2(h0, h1);
-          reinterpret_cast<float2*>(lr)[q] = make_float2(l0, l1);
+        for (int u = 0; u < U; ++u) {
+          const int q = q0 + u * 32 + lane;
+          if (q < full) v[u] = __ldcs(reinterpret_cast<const double2*>(xr) + q);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = q0 + u * 32 + lane;
+          if (q < full) {
+            float h0, l0, h1, l1;
+            split_f32(v[u].x, h0, l0);
+            split_f32(v[u].y, h1, l1);
+            reinterpret_cast<float2*>(hr)[q] = make_float2(h0, h1);
+            reinterpret_cast<float2*>(lr)[q] = make_float2(l0, l1);
+            if (CM) {
+              mx[s][u][0] = max(mx[s][u][0], (unsigned)__double2hiint(v[u].x) & 0x7FFFFFFFu);
+              mx[s][u][1] = max(mx[s][u][1], (unsigned)__double2hiint(v[u].y) & 0x7FFFFFFFu);
+            }
+          }
         }
       }
     }
     if ((d & 1) && lane == 0) {
+      const double x = xr[d - 1];
       float h, l;
-      split_f32(xr[d - 1], h, l);
+      split_f32(x, h, l);
       hr[d - 1] = h;
       lr[d - 1] = l;
+      if (CM) {
+        mtail = max(mtail, (unsigned)__double2hiint(x) & 0x7FFFFFFFu);
+      }
     }
+    if (CM && lane == 1) {
+      my = max(my, (unsigned)__double2hiint(Y[i]) & 0x7FFFFFFFu);
+    }
+  }
+  if (CM) {
+    __syncthreads();   // smax cleared
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = s * 32 * U + u * 32 + lane;
+        if (q < full) {
+          if (mx[s][u][0]) atomicMax(&smax[2 * q], mx[s][u][0]);
+          if (mx[s][u][1]) atomicMax(&smax[2 * q + 1], mx[s][u][1]);
+        }
+      }
+    if (mtail) atomicMax(&smax[d - 1], mtail);
+    if (my) atomicMax(&smax[d], my);
+    __syncthreads();
+    for (int c = threadIdx.x; c <= d; c += blockDim.x)
+      if (smax[c]) atomicMax(colmax + c, (unsigned long long)smax[c] << 32);
   }
 }
 
-// Resident CTAs per SM of k_to_f32 on the current device, computed once per
-// device (the answer depends on the device's limits; a racing first call on
-// two threads computes the same value twice).
+// Resident CTAs per SM of k_to_f32<CM> on the current device, computed once
+// per device and variant (the answer depends on the device's limits; a racing
+// first call on two threads computes the same value twice).
+template <bool CM>
 static int to_f32_blocks_per_sm() {
   static std::atomic<int> per_dev[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
   int v = per_dev[dev].load(std::memory_order_relaxed);
   if (v > 0) return v;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_to_f32, 256, 0) != cudaSuccess || v < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_to_f32<CM>, 256, 0) != cudaSuccess ||
+      v < 1) {
     (void)cudaGetLastError();
     return 1;
   }
@@ -711,9 +771,23 @@ static int to_f32_blocks_per_sm() {
 
 spcg_status launch_to_f32(spcg_ctx* c) {
   // one wave of resident CTAs: the grid-stride loop then has no tail wave
-  k_to_f32<<<to_f32_blocks_per_sm() * c->num_sms, 256, 0, c->stream>>>(
-      c->X, c->ldx, c->N, c->d, c->Xf, c->Xl, c->ldxf);
+  k_to_f32<false><<<to_f32_blocks_per_sm<false>() * c->num_sms, 256, 0, c->stream>>>(
+      c->X, c->ldx, c->N, c->d, c->Xf, c->Xl, c->ldxf, nullptr, nullptr);
   SPCG_CK(cudaGetLastError());
+  c->n_launch += 1;
+  return SPCG_OK;
+}
+
+// The split and the column maxima of the next sketch in one read of X; the
+// next launch_colscales (within the same spcg_sketch call) then skips k_colmax.
+spcg_status launch_to_f32_colmax(spcg_ctx* c) {
+  Sketch& s = c->sk;
+  SPCG_CK(cudaMemsetAsync(s.colmax, 0, (size_t)(c->d + 1) * sizeof(unsigned long long),
+                          c->stream));
+  k_to_f32<true><<<to_f32_blocks_per_sm<true>() * c->num_sms, 256, 0, c->stream>>>(
+      c->X, c->ldx, c->N, c->d, c->Xf, c->Xl, c->ldxf, c->Y, s.colmax);
+  SPCG_CK(cudaGetLastError());
+  s.colmax_pre = true;
   c->n_launch += 1;
   return SPCG_OK;
 }
@@ -731,8 +805,8 @@ extern "C" spcg_status spcg_split_f32(const double* X, int64_t N, int32_t d, int
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return SPCG_E_CUDA;
-  spcg::k_to_f32<<<spcg::to_f32_blocks_per_sm() * sms, 256, 0, (cudaStream_t)stream>>>(
-      X, ldx, N, d, Xh, Xl, ldxf);
+  spcg::k_to_f32<false><<<spcg::to_f32_blocks_per_sm<false>() * sms, 256, 0, (cudaStream_t)stream>>>(
+      X, ldx, N, d, Xh, Xl, ldxf, nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SPCG_E_CUDA;
   return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? SPCG_OK : SPCG_E_CUDA;
 }

@@ -66,6 +66,7 @@ struct PcgBuffers {
 
 struct Sketch {
   bool ready = false;
+  bool colmax_pre = false;   // colmax already holds this call's maxima (fused split)
   uint64_t seed = 0;
   spcg_schedule sched{};
   int64_t n_pad = 0;
@@ -182,6 +183,7 @@ spcg_status launch_colscales(spcg_ctx* c);
 spcg_status launch_countsketch(spcg_ctx* c);
 spcg_status launch_export_rows(spcg_ctx* c, int64_t row0, int64_t n, double* A, double* b);
 spcg_status launch_to_f32(spcg_ctx* c);   // X -> Xf
+spcg_status launch_to_f32_colmax(spcg_ctx* c);   // X -> Xf and the sketch's column maxima
 // qr.cu
 constexpr int kQrPanel = 32;   // panel width of the blocked QR
 spcg_status launch_precond_factor(spcg_ctx* c);

@@ -895,10 +895,14 @@ spcg_status launch_reduce(spcg_ctx* c, double* out, const double* dotvec) {
   return SPCG_OK;
 }
 
-// CTAs of k_dspace: about eight columns (and rows) per CTA, at most one per SM.
+// CTAs of k_dspace: spcg_opts.dspace_ctas when set, else about eight columns
+// (and rows) per CTA; at most one per SM and one per column.  (One CTA with R
+// and R^{-1} staged in shared memory and no grid barrier was slower at every
+// d measured, 40 to 200: the spread CTAs overlap more of the loads.)
 int dspace_grid(const spcg_ctx* c) {
-  int g = (c->d + 7) / 8;
+  int g = c->opts.dspace_ctas > 0 ? c->opts.dspace_ctas : (c->d + 7) / 8;
   if (g > c->num_sms) g = c->num_sms;
+  if (g > c->d) g = c->d;
   return g < 1 ? 1 : g;
 }
 

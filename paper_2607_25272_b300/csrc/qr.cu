@@ -194,6 +194,7 @@ constexpr int QLD = QB + 1;            // row stride of the panel slice in share
 constexpr int QCOLB = 8;               // columns per batch in the T^T W phase
 constexpr int QUNR = 8;                // independent loads in flight per thread in the sums
 constexpr int kQrPanelRows = 48;       // rows per panel CTA (default panel group size)
+constexpr int QRR = 4;                 // rows per step of the trailing-update loops
 
 struct QrCoopArgs {
   double* A;           // r x d column-major (ld = r), reduced in place
@@ -360,16 +361,22 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
     }
     for (int e = tid; e < QB * QB; e += QT) T[e] = a.Tg[e];
     __syncthreads();
-    // W partial = V_own^T C_own
+    // W partial = V_own^T C_own (QRR rows of the column loaded at a time)
     for (int c = tid; c < nt; c += QT) {
       double w[QB];
 #pragma unroll
       for (int i = 0; i < QB; ++i) w[i] = 0.0;
       const double* col = a.A + (int64_t)(k0 + bw + c) * r + lo;
-      for (int ri = 0; ri < nr; ++ri) {
-        const double cv = col[ri];
+      for (int ri0 = 0; ri0 < nr; ri0 += QRR) {
+        double cv[QRR];
 #pragma unroll
-        for (int i = 0; i < QB; ++i) w[i] = fma(P[ri * QLD + i], cv, w[i]);
+        for (int u = 0; u < QRR; ++u) cv[u] = ri0 + u < nr ? col[ri0 + u] : 0.0;
+#pragma unroll
+        for (int u = 0; u < QRR; ++u) {
+          if (ri0 + u >= nr) break;   // uniform over the CTA
+#pragma unroll
+          for (int i = 0; i < QB; ++i) w[i] = fma(P[(ri0 + u) * QLD + i], cv[u], w[i]);
+        }
       }
       double* dst = a.Wp + (size_t)q * QB * d + c;
 #pragma unroll
@@ -406,17 +413,25 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
       }
     }
     if (!grid_sync_bounded(a.bar, a.status, a.spin, &s_fail)) return;
-    // C_own -= V_own W'
+    // C_own -= V_own W': QRR rows at a time, so that QRR independent chains
+    // of multiply-adds keep the FP64 pipe busy
     for (int c = tid; c < nt; c += QT) {
       double wt[QB];
 #pragma unroll
       for (int i = 0; i < QB; ++i) wt[i] = a.Wt[(size_t)i * d + c];
       double* col = a.A + (int64_t)(k0 + bw + c) * r + lo;
-      for (int ri = 0; ri < nr; ++ri) {
-        double acc = col[ri];
+      for (int ri0 = 0; ri0 < nr; ri0 += QRR) {
+        double acc[QRR];
 #pragma unroll
-        for (int i = 0; i < QB; ++i) acc = fma(-P[ri * QLD + i], wt[i], acc);
-        col[ri] = acc;
+        for (int u = 0; u < QRR; ++u) acc[u] = ri0 + u < nr ? col[ri0 + u] : 0.0;
+#pragma unroll
+        for (int i = 0; i < QB; ++i)
+#pragma unroll
+          for (int u = 0; u < QRR; ++u)
+            acc[u] = fma(-P[(ri0 + u < nr ? ri0 + u : 0) * QLD + i], wt[i], acc[u]);
+#pragma unroll
+        for (int u = 0; u < QRR; ++u)
+          if (ri0 + u < nr) col[ri0 + u] = acc[u];
       }
     }
     if (!grid_sync_bounded(a.bar, a.status, a.spin, &s_fail)) return;

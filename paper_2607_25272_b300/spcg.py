@@ -91,6 +91,7 @@ class Opts(ctypes.Structure):
         ("fwht_tile", ctypes.c_int32),
         ("fwht_first_levels", ctypes.c_int32),
         ("qr_panel_ctas", ctypes.c_int32),
+        ("dspace_ctas", ctypes.c_int32),
     ]
 
 

@@ -96,8 +96,9 @@ def test_struct_layouts_match_header_sizes():
     # spcg_schedule: int32 K, int64 m[40], int32 a[40], int64 r, double tol, 2 x int32
     assert ctypes.sizeof(S.Schedule) == 8 + 8 * 40 + 4 * 40 + 8 + 8 + 8 + 8
     # spcg_opts: int32 precision, grid_ctas; int64 spin_budget; 4 x int32; int64 cap;
-    # int32 qr_by_column, fwht_tile, fwht_first_levels, qr_panel_ctas
-    assert ctypes.sizeof(S.Opts) == 4 + 4 + 8 + 16 + 8 + 16
+    # int32 qr_by_column, fwht_tile, fwht_first_levels, qr_panel_ctas, dspace_ctas
+    # (+ 4 bytes of tail padding to the int64 alignment)
+    assert ctypes.sizeof(S.Opts) == 4 + 4 + 8 + 16 + 8 + 20 + 4
 
 
 def test_struct_layouts_match_a_c_compiler(tmp_path):

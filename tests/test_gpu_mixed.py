@@ -25,7 +25,7 @@ from oracle import srht as OR
 from oracle import spcg as OS
 from oracle.metrics import rel_pred_error
 from paper_2607_25272_b300 import spcg as S
-from paper_2607_25272_b300.inputs import gaussian_problem, svd_problem
+from paper_2607_25272_b300.inputs import gaussian_problem, scaled_columns_problem, svd_problem
 
 pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
@@ -239,7 +239,32 @@ def _split_cases():
     return np.concatenate(parts)
 
 
-@pytest.mark.parametrize("d", [1, 7, 64, 257])
+@pytest.mark.parametrize("N,d", [(5000, 37), (20000, 50), (70000, 129), (9000, 300)])
+def test_split_fused_column_maxima_give_the_same_sketch(N, d):
+    """A mixed solve takes the column maxima of the fixed-point scales from its
+    FP32 split; a bare spcg_sketch computes them in a pass of its own.  Both
+    must give the same scales, hence the same sketch and R, bit for bit
+    (columns spanning 1e-3..1e3, negative extremes, an odd last column)."""
+    X, Y, _ = scaled_columns_problem(N, d, 1e-3, 1e3, 0.5, seed=d)
+    X[:, 0] = -np.abs(X[:, 0])               # the largest magnitude is negative
+    Y = -3.0 * Y
+    s = S.Solver(cuda(X), cuda(Y), mixed_opts())
+    sc = S.spcg_default_schedule(N, d)
+    sc.tol = 1e-6
+    s.solve(3, sc, raise_on_error=False)   # the sketch is what is compared
+    mK = sc.m[sc.K - 1] if sc.K else 1
+    A1, b1 = (t.cpu().numpy() for t in s.export_sketch(0, mK))
+    R1 = s.export_precond()[0].cpu().numpy()
+    s.sketch(3, sc)
+    A2, b2 = (t.cpu().numpy() for t in s.export_sketch(0, mK))
+    R2 = s.export_precond()[0].cpu().numpy()
+    s.close()
+    assert np.array_equal(A1.view(np.uint64), A2.view(np.uint64))
+    assert np.array_equal(b1.view(np.uint64), b2.view(np.uint64))
+    assert np.array_equal(R1.view(np.uint64), R2.view(np.uint64))
+
+
+@pytest.mark.parametrize("d", [1, 7, 64, 257, 1100])
 def test_split_f32_is_round_to_nearest(d):
     """Xh = fl32(x), Xl = fl32(x - Xh), bit for bit against numpy's rounding."""
     v = _split_cases()

@@ -248,15 +248,23 @@ def test_qr_blocked_and_per_column_agree(N, d, r, seed):
 
 
 # ---------------------------------------------------------------- stages ----
-@pytest.mark.parametrize("N,d,kappa,seed", [(20000, 50, None, 1), (30000, 24, 1e4, 3)])
-def test_stage_iterates_match_oracle(N, d, kappa, seed):
+@pytest.mark.parametrize("N,d,kappa,seed,ds", [(20000, 50, None, 1, 0), (20000, 50, None, 1, 4),
+                                               (30000, 24, 1e4, 3, 0), (30000, 24, 1e4, 3, 2),
+                                               (12000, 96, 1e3, 4, 0), (12000, 96, 1e3, 4, 12),
+                                               (12000, 97, 1e3, 4, 0), (12000, 97, 1e3, 4, 1)])
+def test_stage_iterates_match_oracle(N, d, kappa, seed, ds):
+    """Every stage's iterate against the oracle's PCG at 1e-10, with the d-space
+    step in one CTA (shared-memory kernel up to d = 96, else the cooperative
+    kernel on one CTA) or spread over several CTAs (ds = spcg_opts.dspace_ctas)."""
     if kappa is None:
         X, Y, _ = gaussian_problem(N, d, 1.0, seed=seed)
     else:
         X, Y, _ = svd_problem(N, d, kappa, 0.1, seed=seed)
     sched = OS.default_schedule(N, d)
     stages, A_hat, R = OS.sketch_all(X, Y, seed, sched)
-    s = S.Solver(cuda(X), cuda(Y))
+    o = S.Opts()
+    o.dspace_ctas = ds
+    s = S.Solver(cuda(X), cuda(Y), o)
     s.sketch(seed, S.spcg_default_schedule(N, d))
     beta_g = torch.zeros(d, dtype=torch.float64, device="cuda")
     beta_o = np.zeros(d)
@@ -285,7 +293,8 @@ def test_solve_gaussian_c1(tol):
 
 
 @pytest.mark.parametrize("N,d,kappa,sigma,seed", [(16384, 40, 1e6, 0.1, 2), (5000, 37, 1e3, 1.0, 6),
-                                                  (70000, 129, 1e5, 0.5, 8)])
+                                                  (70000, 129, 1e5, 0.5, 8), (5000, 1, 1.0, 1.0, 9),
+                                                  (6000, 2, 1e2, 1.0, 10)])
 def test_solve_ill_conditioned_ragged(N, d, kappa, sigma, seed):
     X, Y, _ = svd_problem(N, d, kappa, sigma, seed=seed)
     bh = OL.ols(X, Y)
