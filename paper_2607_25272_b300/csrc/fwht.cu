@@ -282,11 +282,10 @@ __global__ void __launch_bounds__(512) k_fwht_pass(const FwhtArgs a) {
   for (int c = tid; c < TC; c += NT) sh[c] = (c0 + c < a.C) ? a.shift[c0 + c] : 0;
   if (a.first)
     for (int t = tid; t < L; t += NT) gmap[t] = (int32_t)a.gather[grow(t)];
-  if (a.last)
+  if (a.last)   // the maps are stored in the last pass's row order
     for (int t = tid; t < L; t += NT) {
-      const int64_t j = grow(t);
-      dmap[t] = a.dest[j];
-      hmap[t] = a.hdest[j];
+      dmap[t] = a.dest[base * L + t];
+      hmap[t] = a.hdest[base * L + t];
     }
   __syncthreads();
 
@@ -375,10 +374,10 @@ __global__ void __launch_bounds__(TileShape<LOGL, V>::NT, TileShape<LOGL, V>::MI
   const int sh = colok ? a.shift[col] : 0;
   if (a.first)
     for (int t = tid; t < L; t += S::NT) gmap[t] = (int32_t)a.gather[j0 + t * step];
-  if (a.last)
+  if (a.last)   // the maps are stored in the last pass's row order
     for (int t = tid; t < L; t += S::NT) {
-      dmap[t] = a.dest[j0 + t * step];
-      hmap[t] = a.hdest[j0 + t * step];
+      dmap[t] = a.dest[base * L + t];
+      hmap[t] = a.hdest[base * L + t];
     }
   __syncthreads();
   long long v[VPT];

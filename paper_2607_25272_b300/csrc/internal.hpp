@@ -178,6 +178,10 @@ spcg_status from_cuda(cudaError_t e);
 spcg_status launch_sketch_maps(spcg_ctx* c);
 // fwht.cu
 spcg_status launch_transform(spcg_ctx* c);
+// Split n index bits into transform passes of at most 12 bits; returns the
+// number of passes and their levels in logl[] (first_levels > 0 fixes the
+// first of a two-pass plan).
+int fwht_pass_plan(int n, int* logl, int first_levels);
 spcg_status launch_colscales(spcg_ctx* c);
 // countsketch.cu
 spcg_status launch_countsketch(spcg_ctx* c);

@@ -1211,11 +1211,17 @@ __global__ void __launch_bounds__(DfCfg<NI>::THREADS, 1)
     }
   } else {
     const int cw = warp - 1;
+    // Rows up to 512 wide (BF): lanes whose columns lie past d read the row's
+    // first columns instead; the direction is zero there, so the row products
+    // are unchanged, and their column sums are never written, so the row
+    // loops have no branch (6-8 % faster).  Wider rows skip those columns
+    // with a branch: without it their 128 registers spill.
+    constexpr bool BF = NI <= 16;
     int off[NG];
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
       const int c0 = g * 32 * V + lane * V;
-      off[g] = (c0 < a.d) ? (c0 / a.boxc) * (int)a.slot_elems + (c0 % a.boxc) : -1;
+      off[g] = (c0 < a.d) ? (c0 / a.boxc) * (int)a.slot_elems + (c0 % a.boxc) : (BF ? 0 : -1);
     }
     float ph[PREG ? NG : 1][V], pl[PREG ? NG : 1][V];
     if constexpr (PREG) {
@@ -1247,7 +1253,7 @@ __global__ void __launch_bounds__(DfCfg<NI>::THREADS, 1)
         float sh = 0.f, sl = 0.f;   // x . v in double-FP32
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
-          if (off[g] < 0) continue;
+          if (!BF && off[g] < 0) continue;
           const float4 h4 = *reinterpret_cast<const float4*>(rh + off[g]);
           const float4 l4 = *reinterpret_cast<const float4*>(rl + off[g]);
           const float xa[V] = {h4.x, h4.y, h4.z, h4.w}, xb[V] = {l4.x, l4.y, l4.z, l4.w};
@@ -1312,7 +1318,7 @@ __global__ void __launch_bounds__(DfCfg<NI>::THREADS, 1)
         }
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
-          if (off[g] < 0) continue;
+          if (!BF && off[g] < 0) continue;
           float xa[V], xb[V];
           if constexpr (XCACHE) {
 #pragma unroll

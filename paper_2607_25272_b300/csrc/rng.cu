@@ -38,18 +38,24 @@ __global__ void k_signs(uint64_t seed, int64_t n, double* __restrict__ out) {
 //   gather[j] = P(j) with bit 31 set when D_j = -1 ((D P X')_j = D_j X'_{P(j)})
 //   dest[j]   = pi^{-1}(j) if it is < m_K (row j belongs to I_K), else -1
 //   hdest[j]  = sigma_hat^{-1}(j) if it is < r (row j belongs to I-hat), else -1
+// dest and hdest are stored in the row order of the transform's last pass
+// (its rows j = low + t 2^last_shift, t < 2^last_logl, at index
+// low 2^last_logl + t), so that the pass reads its tile's entries
+// contiguously; with one pass that order is j itself.
 __global__ void k_sketch_maps(int nbits, uint64_t seed, int64_t n_pad, int64_t mK, int64_t r,
-                              uint32_t* __restrict__ gather, int32_t* __restrict__ dest,
-                              int32_t* __restrict__ hdest) {
+                              int last_shift, int last_logl, uint32_t* __restrict__ gather,
+                              int32_t* __restrict__ dest, int32_t* __restrict__ hdest) {
+  const int64_t low_mask = (int64_t(1) << last_shift) - 1;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_pad;
        j += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t src = feistel((uint32_t)j, nbits, TAG_P, seed, false);
     const int sgn = rademacher((uint64_t)j, seed);
     gather[j] = src | (sgn < 0 ? 0x80000000u : 0u);
+    const int64_t jl = ((j & low_mask) << last_logl) | (j >> last_shift);
     const uint32_t t = feistel((uint32_t)j, nbits, TAG_PI, seed, true);
-    dest[j] = ((int64_t)t < mK) ? (int32_t)t : -1;
+    dest[jl] = ((int64_t)t < mK) ? (int32_t)t : -1;
     const uint32_t th = feistel((uint32_t)j, nbits, TAG_HAT, seed, true);
-    hdest[j] = ((int64_t)th < r) ? (int32_t)th : -1;
+    hdest[jl] = ((int64_t)th < r) ? (int32_t)th : -1;
   }
 }
 
@@ -63,8 +69,11 @@ static int grid_for(int64_t n, int threads) {
 spcg_status launch_sketch_maps(spcg_ctx* c) {
   Sketch& s = c->sk;
   const int64_t mK = s.sched.K > 0 ? s.sched.m[s.sched.K - 1] : 0;
+  int logl[8];
+  const int passes = fwht_pass_plan(s.nbits, logl, c->opts.fwht_first_levels);
+  const int last_logl = logl[passes - 1], last_shift = s.nbits - last_logl;
   k_sketch_maps<<<grid_for(s.n_pad, 256), 256, 0, c->stream>>>(
-      s.nbits, s.seed, s.n_pad, mK, s.sched.r, s.gather, s.dest, s.hdest);
+      s.nbits, s.seed, s.n_pad, mK, s.sched.r, last_shift, last_logl, s.gather, s.dest, s.hdest);
   SPCG_CK(cudaGetLastError());
   c->n_launch += 1;
   return SPCG_OK;
