@@ -173,6 +173,38 @@ def test_sketch_rows_and_preconditioner(N, d, seed, r):
     s.close()
 
 
+# Stage sizes that are not powers of two keep the prefix in nested order (the
+# bucketed storage needs power-of-two stages): rows against the oracle, and
+# every stage iterate against the oracle's PCG on the same rows.
+def test_sketch_and_stages_with_uneven_stage_sizes():
+    N, d, seed = 40000, 50, 13
+    X, Y, _ = svd_problem(N, d, 1e3, 0.1, seed=seed)
+    sched = OS.default_schedule(N, d)
+    sched["m"], sched["a"] = [3000, 7000, 12000], [3, 3, 3]
+    sc = S.spcg_default_schedule(N, d)
+    sc.K = 3
+    for i, (m, a) in enumerate(zip(sched["m"], sched["a"])):
+        sc.m[i], sc.a[i] = m, a
+    s = S.Solver(cuda(X), cuda(Y))
+    s.sketch(seed, sc)
+    n_pad = sched["n_pad"]
+    ZX, ZY, stages, A_hat = _oracle_sketch(X, Y, seed, sched)
+    mK = sched["m"][-1]
+    A_g, b_g = (t.cpu().numpy() for t in s.export_sketch(0, mK))
+    pi = OR.nested_order(n_pad, mK, seed)
+    Zo = np.concatenate([ZX[pi], ZY[pi][:, None]], axis=1)
+    Zg = np.concatenate([A_g, b_g[:, None]], axis=1)
+    assert np.all(np.abs(Zg - Zo) <= _transform_tol(X, Y, n_pad, Zo))
+    R = OL.r_factor(A_hat)
+    beta_g = torch.zeros(d, dtype=torch.float64, device="cuda")
+    beta_o = np.zeros(d)
+    for i, ((A_i, b_i), a_i) in enumerate(zip(stages, sched["a"])):
+        beta_o, _ = OS.pcg(A_i, b_i, R, beta_o, a_i)
+        s.pcg_stage(i, a_i, beta_g)
+        assert rel_pred_error(X, beta_g.cpu().numpy(), beta_o) <= 1e-10, i
+    s.close()
+
+
 # The transform's kernels and pass plans: the 64-bit fixed-point butterflies
 # are exact, so every tile variant and every split of the index bits into two
 # passes must give the same bits; one of them is checked against the oracle's
