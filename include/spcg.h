@@ -125,10 +125,12 @@ typedef struct {
                                beta); an allocation by spcg_create or
                                spcg_sketch that would pass it fails with
                                SPCG_E_OOM before any cudaMalloc; 0 = no cap   */
-  int32_t qr_by_column;     /* 1 = factor the preconditioner sketch with one
-                               launch per Householder step instead of the
-                               blocked cooperative QR (same factorisation,
-                               slower; for comparison)                         */
+  int32_t qr_by_column;     /* preconditioner QR: 0 = blocked, with look-ahead
+                               from d = 256 on (a panel group factors panel p
+                               while the other CTAs apply panel p-1 to the
+                               later columns), 1 = one launch per Householder
+                               step, 2 = blocked without look-ahead (same
+                               factorisation; 1 and 2 for comparison)          */
   int32_t fwht_tile;        /* transform passes of 9..12 levels: 0 = default
                                (the per-round pass kernel, as 3), 1 = 128 KB
                                tiles, one CTA per SM, 2 = 64 KB tiles, two CTAs
@@ -137,8 +139,9 @@ typedef struct {
   int32_t fwht_first_levels; /* levels of the first of two transform passes;
                                0 = split evenly                               */
   int32_t qr_panel_ctas;    /* CTAs that factor each 32-column panel of the
-                               preconditioner QR; 0 = about one per 48 rows of
-                               the sketch (at most one per SM)                 */
+                               preconditioner QR; 0 = about 30000 / d, at most
+                               half the grid (with look-ahead), or one per 48
+                               rows of the sketch (without)                    */
   int32_t dspace_ctas;      /* CTAs of the per-iteration d-space step (alpha,
                                g, beta, z = R^{-1} R^{-T} g and its dots, one
                                cooperative launch); 0 = about one per 8

@@ -58,8 +58,9 @@ static spcg_status qr_alloc(spcg_ctx* c) {
   SPCG_TRY(dalloc(c, &s.qr_red, (size_t)2 * G * 2 * kQrPanel));
   SPCG_TRY(dalloc(c, &s.qr_wp, (size_t)G * kQrPanel * d));
   SPCG_TRY(dalloc(c, &s.qr_wt, (size_t)kQrPanel * d));
-  SPCG_TRY(dalloc(c, &s.qr_tg, (size_t)kQrPanel * kQrPanel));
-  SPCG_TRY(dalloc(c, &s.qr_bar, (size_t)2 * kBarWords));
+  SPCG_TRY(dalloc(c, &s.qr_tg, (size_t)2 * kQrPanel * kQrPanel));
+  SPCG_TRY(dalloc(c, &s.qr_wl, (size_t)(G + 1) * kQrPanel * kQrPanel));
+  SPCG_TRY(dalloc(c, &s.qr_bar, (size_t)3 * kBarWords));
   return SPCG_OK;
 }
 
@@ -476,7 +477,8 @@ static spcg_status create_impl(const double* X, const double* Y, int64_t N, int3
     return fail(SPCG_E_INVALID_ARG);
   if (c->opts.fwht_tile < 0 || c->opts.fwht_tile > 3 || c->opts.fwht_first_levels < 0 ||
       c->opts.fwht_first_levels > 12 || c->opts.max_workspace_bytes < 0 ||
-      c->opts.qr_panel_ctas < 0 || c->opts.dspace_ctas < 0)
+      c->opts.qr_panel_ctas < 0 || c->opts.dspace_ctas < 0 || c->opts.qr_by_column < 0 ||
+      c->opts.qr_by_column > 2)
     return fail(SPCG_E_INVALID_ARG);
   if (c->opts.precision == SPCG_PREC_MIXED) {
     c->ldxf = (d + 3) & ~int64_t(3);
@@ -515,6 +517,7 @@ extern "C" void spcg_destroy(spcg_ctx* c) {
   dfree(c, c->sk.qr_vdiag);
   dfree(c, c->sk.qr_red);
   dfree(c, c->sk.qr_wp);
+  dfree(c, c->sk.qr_wl);
   dfree(c, c->sk.qr_wt);
   dfree(c, c->sk.qr_bar);
   dfree(c, c->sk.qr_tg);

@@ -96,8 +96,9 @@ struct Sketch {
   double* qr_red = nullptr;     // 2 x SMs x (2 x panel width): per-CTA partial sums
   double* qr_wp = nullptr;      // SMs x panel width x d: per-CTA partials of V^T C
   double* qr_wt = nullptr;      // panel width x d: T^T V^T C
-  double* qr_tg = nullptr;      // panel width^2: T of the current panel
-  unsigned* qr_bar = nullptr;   // 2 barriers of kBarWords (grid, panel group)
+  double* qr_tg = nullptr;      // 2 x panel width^2: T of the current (and previous) panel
+  double* qr_wl = nullptr;      // (SMs + 1) x panel width^2: look-ahead partials of V^T C
+  unsigned* qr_bar = nullptr;   // 3 barriers of kBarWords (grid, panel group, update group)
   unsigned long long* colmax = nullptr;  // d + 1: largest |x| per column (bit pattern)
   int* colshift = nullptr;      // d + 1: fixed-point scale exponent per column
   PassGeom geom[SPCG_MAX_STAGES];  // fused-pass geometry of stage i

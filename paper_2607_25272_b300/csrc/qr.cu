@@ -195,6 +195,8 @@ constexpr int QCOLB = 8;               // columns per batch in the T^T W phase
 constexpr int QUNR = 8;                // independent loads in flight per thread in the sums
 constexpr int kQrPanelRows = 48;       // rows per panel CTA (default panel group size)
 constexpr int QRR = 4;                 // rows per step of the trailing-update loops
+constexpr int kQrLaPanelWork = 30000;  // look-ahead QR: panel CTAs = this / d (default)
+constexpr int kQrLaMinD = 256;         // look-ahead QR from this many columns (eight panels)
 
 struct QrCoopArgs {
   double* A;           // r x d column-major (ld = r), reduced in place
@@ -438,6 +440,359 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Blocked QR with look-ahead, one cooperative launch.  The grid is split in
+// two groups that work at the same time on every panel p:
+//   panel group (CTAs [0, GP), rows of the panel split among them): applies
+//     panel p-1's reflectors to panel p's columns (W = V^T C summed over the
+//     group, W' = T^T W, C -= V W'; CTA 0 also takes the 32 rows of panel
+//     p-1's block, which hold R entries), then factors panel p as k_qr_coop
+//     does (one group reduction per column step);
+//   update group (CTAs [GP, G), rows split among them): applies panel p-1's
+//     reflectors to every column right of panel p, as k_qr_coop's trailing
+//     update with a barrier of its own.
+// One grid barrier per panel; the latency-bound column steps of panel p run
+// while the FP64-bound update of the columns right of it proceeds.  Panel T
+// factors alternate between two buffers (the update group reads T_{p-1}
+// while the panel group writes T_p).  (An update group that split the columns
+// instead, each column's W = V^T c inside one CTA with V staged 128 rows at a
+// time, was slower: the staging is latency-bound.)
+// ---------------------------------------------------------------------------
+
+struct QrLaArgs {
+  double* A;           // r x d column-major (ld = r), reduced in place
+  int64_t r;
+  int d;
+  int gp;              // CTAs of the panel group
+  int chunk_max;       // largest row slice of a panel CTA
+  double* Tg;          // 2 x QB x QB: T of panel p at Tg + (p & 1) QB QB
+  double* Rdiag;       // d: alpha_k
+  double* vdiag;       // d: v_0 of reflector k
+  double* red;         // 2 x G x QSL: column-step sums of the panel group
+  double* Wl;          // (GP + 1) x QB x QB: look-ahead partials, then their sum
+  double* Wp;          // GU x QB x d: the update group's W partials
+  double* Wt;          // QB x d: W' = T^T W of the update group
+  int chunk_u;         // rows of the largest row slice of an update CTA
+  unsigned* bar;       // grid barrier (zero at launch)
+  unsigned* bar2;      // panel-group barrier (zero at launch)
+  unsigned* bar3;      // update-group barrier (zero at launch)
+  int* status;
+  long long spin;
+};
+
+__global__ void __launch_bounds__(QT, 1) k_qr_la(const QrLaArgs a) {
+  extern __shared__ double qsm[];
+  __shared__ int s_fail;
+  __shared__ double sc[2];
+  __shared__ double fcol[QB];
+  const int tid = threadIdx.x, G = gridDim.x, q = blockIdx.x;
+  if (tid == 0) s_fail = 0;
+  if (*a.status != 0) return;   // uniform: set before this launch
+  __syncthreads();
+  const int64_t r = a.r;
+  const int d = a.d;
+  const int GP = a.gp;
+  const bool panel_cta = q < GP;
+  // panel group layout
+  double* P = qsm;                                   // chunk_max x QLD
+  double* Vo = P + (size_t)a.chunk_max * QLD;        // chunk_max x QLD: V_{p-1}, own rows
+  double* E = Vo + (size_t)a.chunk_max * QLD;        // QB x QLD: rows of panel p-1's block
+  double* VE = E + QB * QLD;                         // QB x QLD: V_{p-1} on those rows
+  double* T = VE + QB * QLD;                         // QB x QB
+  double* W = T + QB * QB;                           // QB x QB
+  double* tot = W + QB * QB;                         // QSL
+  double* comb = tot + QSL;                          // 4 x QSL
+  double* pv0 = comb + 4 * QSL;                      // QB
+  int step = 0;
+  for (int k0 = 0; k0 < d; k0 += QB) {
+    const int p = k0 / QB;
+    const int bw = d - k0 < QB ? d - k0 : QB;
+    const int kp = k0 - QB;   // first column (and row) of panel p-1
+    if (panel_cta) {
+      const int64_t mp = r - k0;
+      const int64_t chunk = (mp + GP - 1) / GP;
+      const int64_t lo = k0 + (int64_t)q * chunk;
+      const int64_t hi = lo + chunk < r ? lo + chunk : r;
+      const int nr = hi > lo ? (int)(hi - lo) : 0;
+      for (int e = tid; e < nr * QB; e += QT) {
+        const int j = e / nr, ri = e % nr;
+        P[ri * QLD + j] = j < bw ? a.A[(int64_t)(k0 + j) * r + lo + ri] : 0.0;
+      }
+      if (p > 0) {
+        // ---- look-ahead: panel p-1's reflectors on panel p's columns ----
+        for (int e = tid; e < nr * QB; e += QT) {   // own rows lie below panel p-1's block
+          const int i = e / nr, ri = e % nr;
+          Vo[ri * QLD + i] = a.A[(int64_t)(kp + i) * r + lo + ri];
+        }
+        if (q == 0)
+          for (int e = tid; e < QB * QB; e += QT) {
+            const int i = e / QB, ee = e % QB;   // row kp + ee, column i of V / j of C
+            const int64_t row = kp + ee;
+            VE[ee * QLD + i] = ee > i ? a.A[(int64_t)(kp + i) * r + row]
+                                      : (ee == i ? a.vdiag[kp + i] : 0.0);
+            E[ee * QLD + i] = i < bw ? a.A[(int64_t)(k0 + i) * r + row] : 0.0;
+          }
+        for (int e = tid; e < QB * QB; e += QT) T[e] = a.Tg[(size_t)((p - 1) & 1) * QB * QB + e];
+        __syncthreads();
+        // partial W = V^T C over own rows (thread: row i of W, four columns)
+        {
+          const int i = tid >> 3, j0 = (tid & 7) * 4;
+          double acc[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int ri = 0; ri < nr; ++ri) {
+            const double v = Vo[ri * QLD + i];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fma(v, P[ri * QLD + j0 + u], acc[u]);
+          }
+          if (q == 0)
+            for (int ee = 0; ee < QB; ++ee) {
+              const double v = VE[ee * QLD + i];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) acc[u] = fma(v, E[ee * QLD + j0 + u], acc[u]);
+            }
+          double* dst = a.Wl + (size_t)q * QB * QB + i * QB + j0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) dst[u] = acc[u];
+        }
+        if (!group_sync_bounded(a.bar2, (unsigned)GP, a.status, a.spin, &s_fail)) return;
+        // W = sum of the partials in CTA order, each CTA a share of the entries
+        {
+          double* Wsum = a.Wl + (size_t)GP * QB * QB;
+          const int per = (QB * QB + GP - 1) / GP;
+          for (int e = q * per + tid; e < (q + 1) * per && e < QB * QB; e += QT) {
+            double acc = 0.0;
+            for (int g0 = 0; g0 < GP; g0 += QUNR) {
+              double v[QUNR];
+#pragma unroll
+              for (int k = 0; k < QUNR; ++k)
+                v[k] = g0 + k < GP ? a.Wl[(size_t)(g0 + k) * QB * QB + e] : 0.0;
+#pragma unroll
+              for (int k = 0; k < QUNR; ++k) acc += v[k];
+            }
+            Wsum[e] = acc;
+          }
+        }
+        if (!group_sync_bounded(a.bar2, (unsigned)GP, a.status, a.spin, &s_fail)) return;
+        {
+          const double* Wsum = a.Wl + (size_t)GP * QB * QB;
+          for (int e = tid; e < QB * QB; e += QT) W[e] = Wsum[e];
+        }
+        __syncthreads();
+        // W' = T^T W, formed in registers and written over W
+        {
+          const int i = tid >> 3, j0 = (tid & 7) * 4;
+          double acc[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int l = 0; l <= i; ++l) {
+            const double t = T[l * QB + i];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fma(t, W[l * QB + j0 + u], acc[u]);
+          }
+          __syncthreads();
+#pragma unroll
+          for (int u = 0; u < 4; ++u) W[i * QB + j0 + u] = acc[u];
+        }
+        __syncthreads();
+        // C -= V W' on own rows (and CTA 0's block rows, written back now)
+        for (int e = tid; e < nr * QB; e += QT) {
+          const int ri = e / QB, j = e % QB;
+          double acc = P[ri * QLD + j];
+          for (int i = 0; i < QB; ++i) acc = fma(-Vo[ri * QLD + i], W[i * QB + j], acc);
+          P[ri * QLD + j] = acc;
+        }
+        if (q == 0)
+          for (int e = tid; e < QB * bw; e += QT) {
+            const int ee = e / bw, j = e % bw;
+            double acc = E[ee * QLD + j];
+            for (int i = 0; i < QB; ++i) acc = fma(-VE[ee * QLD + i], W[i * QB + j], acc);
+            a.A[(int64_t)(k0 + j) * r + kp + ee] = acc;
+          }
+      }
+      for (int e = tid; e < QB * QB; e += QT) T[e] = 0.0;
+      __syncthreads();
+      // ---- factor panel p (as in k_qr_coop) ----
+      for (int j = 0; j < bw; ++j, ++step) {
+        const int64_t diag = k0 + j;
+        const int own = (diag >= lo && diag < hi) ? (int)(diag - lo) : -1;
+        {
+          const int sl = tid % QSL, grp = tid / QSL;
+          double acc = 0.0;
+          if (sl < QB) {
+            if (sl < bw) {
+              int ri0 = (int)(diag + 1 - lo);
+              if (ri0 < 0) ri0 = 0;
+              for (int ri = ri0 + grp; ri < nr; ri += 4) acc = fma(P[ri * QLD + sl], P[ri * QLD + j], acc);
+            }
+          } else if (grp == 0 && own >= 0 && sl - QB < bw) {
+            acc = P[own * QLD + (sl - QB)];
+          }
+          comb[grp * QSL + sl] = acc;
+        }
+        __syncthreads();
+        double* red = a.red + (size_t)(step & 1) * G * QSL;
+        if (tid < QSL)
+          red[(size_t)q * QSL + tid] =
+              ((comb[tid] + comb[QSL + tid]) + comb[2 * QSL + tid]) + comb[3 * QSL + tid];
+        if (!group_sync_bounded(a.bar2, (unsigned)GP, a.status, a.spin, &s_fail)) return;
+        {
+          const int sl = tid % QSL, grp = tid / QSL;
+          double acc = 0.0;
+          for (int g0 = grp; g0 < GP; g0 += 4 * QUNR) {
+            double v[QUNR];
+#pragma unroll
+            for (int k = 0; k < QUNR; ++k) {
+              const int g = g0 + 4 * k;
+              v[k] = g < GP ? red[(size_t)g * QSL + sl] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < QUNR; ++k) acc += v[k];
+          }
+          comb[grp * QSL + sl] = acc;
+        }
+        __syncthreads();
+        if (tid < QSL) tot[tid] = ((comb[tid] + comb[QSL + tid]) + comb[2 * QSL + tid]) + comb[3 * QSL + tid];
+        __syncthreads();
+        if (tid == 0) {
+          const double s2 = tot[j], x0 = tot[QB + j];
+          const double normx = sqrt(fma(x0, x0, s2));
+          const double alpha = (x0 >= 0.0) ? -normx : normx;
+          const double v0 = x0 - alpha;
+          const double vv = fma(v0, v0, s2);
+          pv0[j] = v0;
+          sc[0] = v0;
+          sc[1] = vv > 0.0 ? 2.0 / vv : 0.0;
+          if (q == 0) {
+            a.Rdiag[diag] = alpha;
+            a.vdiag[diag] = v0;
+          }
+        }
+        __syncthreads();
+        const double v0 = sc[0], tau = sc[1];
+        if (tid < j) {
+          double sacc = 0.0;
+          for (int l = tid; l < j; ++l) sacc = fma(T[tid * QB + l], fma(tot[QB + l], v0, tot[l]), sacc);
+          T[tid * QB + j] = -tau * sacc;
+        } else if (tid == j) {
+          T[j * QB + j] = tau;
+        }
+        const int ncl = bw - j - 1;
+        if (tid > j && tid < bw) fcol[tid] = tau * fma(v0, tot[QB + tid], tot[tid]);
+        __syncthreads();
+        for (int e = tid; e < nr * ncl; e += QT) {
+          const int i = j + 1 + e / nr, ri = e % nr;
+          const int64_t row = lo + ri;
+          if (row < diag) continue;
+          const double vr = (row == diag) ? v0 : P[ri * QLD + j];
+          P[ri * QLD + i] = fma(-fcol[i], vr, P[ri * QLD + i]);
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < nr * bw; e += QT) {
+        const int j = e / nr, ri = e % nr;
+        a.A[(int64_t)(k0 + j) * r + lo + ri] = P[ri * QLD + j];
+      }
+      if (q == 0)
+        for (int e = tid; e < QB * QB; e += QT) a.Tg[(size_t)(p & 1) * QB * QB + e] = T[e];
+    } else {
+      step += bw;   // keep the reduction buffers' parity with the panel group
+      // ---- update group: panel p-1's reflectors on the columns right of panel
+      // p, rows kp .. r-1 split among the GU CTAs (as k_qr_coop's trailing
+      // update, with the group's own barrier): W partials, their sum and
+      // W' = T^T W by columns, then C -= V W' on own rows ----
+      const int cstart = k0 + bw;
+      const int nt = d - cstart;
+      if (p > 0 && nt > 0) {
+        const int GU = G - GP, u = q - GP;
+        const int64_t mu = r - kp;
+        const int64_t chunk = (mu + GU - 1) / GU;
+        const int64_t lo = kp + (int64_t)u * chunk;
+        const int64_t hi = lo + chunk < r ? lo + chunk : r;
+        const int nr = hi > lo ? (int)(hi - lo) : 0;
+        double* Pu = qsm;                              // chunk x QLD: V_{p-1}, own rows
+        double* Tu = Pu + (size_t)a.chunk_u * QLD;     // QB x QB
+        double* wsm = Tu + QB * QB;                    // QCOLB x QB
+        for (int e = tid; e < nr * QB; e += QT) {
+          const int i = e / nr, ri = e % nr;
+          const int64_t row = lo + ri;
+          Pu[ri * QLD + i] = row > kp + i ? a.A[(int64_t)(kp + i) * r + row]
+                                          : (row == kp + i ? a.vdiag[kp + i] : 0.0);
+        }
+        for (int e = tid; e < QB * QB; e += QT) Tu[e] = a.Tg[(size_t)((p - 1) & 1) * QB * QB + e];
+        __syncthreads();
+        for (int c = tid; c < nt; c += QT) {
+          double w[QB];
+#pragma unroll
+          for (int i = 0; i < QB; ++i) w[i] = 0.0;
+          const double* col = a.A + (int64_t)(cstart + c) * r + lo;
+          for (int ri0 = 0; ri0 < nr; ri0 += QRR) {
+            double cv[QRR];
+#pragma unroll
+            for (int k = 0; k < QRR; ++k) cv[k] = ri0 + k < nr ? col[ri0 + k] : 0.0;
+#pragma unroll
+            for (int k = 0; k < QRR; ++k) {
+              if (ri0 + k >= nr) break;   // uniform over the CTA
+#pragma unroll
+              for (int i = 0; i < QB; ++i) w[i] = fma(Pu[(ri0 + k) * QLD + i], cv[k], w[i]);
+            }
+          }
+          double* dst = a.Wp + (size_t)u * QB * d + c;
+#pragma unroll
+          for (int i = 0; i < QB; ++i) dst[(size_t)i * d] = w[i];
+        }
+        if (!group_sync_bounded(a.bar3, (unsigned)GU, a.status, a.spin, &s_fail)) return;
+        {
+          const int cs = (nt + GU - 1) / GU;
+          const int c_lo = u * cs, c_hi = c_lo + cs < nt ? c_lo + cs : nt;
+          for (int cb = c_lo; cb < c_hi; cb += QCOLB) {
+            const int ncb = c_hi - cb < QCOLB ? c_hi - cb : QCOLB;
+            for (int e = tid; e < ncb * QB; e += QT) {
+              const int cc = e / QB, i = e % QB;
+              double acc = 0.0;
+              const double* src = a.Wp + (size_t)i * d + cb + cc;
+              for (int g0 = 0; g0 < GU; g0 += QUNR) {
+                double v[QUNR];
+#pragma unroll
+                for (int k = 0; k < QUNR; ++k) v[k] = g0 + k < GU ? src[(size_t)(g0 + k) * QB * d] : 0.0;
+#pragma unroll
+                for (int k = 0; k < QUNR; ++k) acc += v[k];
+              }
+              wsm[cc * QB + i] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < ncb * QB; e += QT) {
+              const int cc = e / QB, i = e % QB;
+              double acc = 0.0;
+              for (int l = 0; l <= i; ++l) acc = fma(Tu[l * QB + i], wsm[cc * QB + l], acc);
+              a.Wt[(size_t)i * d + cb + cc] = acc;
+            }
+            __syncthreads();
+          }
+        }
+        if (!group_sync_bounded(a.bar3, (unsigned)GU, a.status, a.spin, &s_fail)) return;
+        for (int c = tid; c < nt; c += QT) {
+          double wt[QB];
+#pragma unroll
+          for (int i = 0; i < QB; ++i) wt[i] = a.Wt[(size_t)i * d + c];
+          double* col = a.A + (int64_t)(cstart + c) * r + lo;
+          for (int ri0 = 0; ri0 < nr; ri0 += QRR) {
+            double acc[QRR];
+#pragma unroll
+            for (int k = 0; k < QRR; ++k) acc[k] = ri0 + k < nr ? col[ri0 + k] : 0.0;
+#pragma unroll
+            for (int i = 0; i < QB; ++i)
+#pragma unroll
+              for (int k = 0; k < QRR; ++k)
+                acc[k] = fma(-Pu[(ri0 + k < nr ? ri0 + k : 0) * QLD + i], wt[i], acc[k]);
+#pragma unroll
+            for (int k = 0; k < QRR; ++k)
+              if (ri0 + k < nr) col[ri0 + k] = acc[k];
+          }
+        }
+      }
+    }
+    if (k0 + bw >= d) break;   // last panel factored
+    if (!grid_sync_bounded(a.bar, a.status, a.spin, &s_fail)) return;
+  }
+}
+
 // R (row-major upper, diag > 0) from the reduced matrix: row i of R is row i
 // of A after step i, times the sign that makes alpha_i positive.
 __global__ void k_extract_R(const double* __restrict__ A, int64_t r, int d,
@@ -539,6 +894,12 @@ static size_t qr_coop_smem(int64_t chunk_max) {
   return ((size_t)chunk_max * QLD + QB * QB + QSL + 4 * QSL + QB + QCOLB * QB) * sizeof(double);
 }
 
+static size_t qr_la_smem(int64_t chunk_max, int64_t chunk_u) {
+  const size_t panel = (size_t)2 * chunk_max * QLD + 2 * QB * QLD + 2 * QB * QB + QSL + 4 * QSL + QB;
+  const size_t update = (size_t)chunk_u * QLD + QB * QB + QCOLB * QB;
+  return (panel > update ? panel : update) * sizeof(double);
+}
+
 // The per-column fallback (one launch per Householder step).
 static spcg_status householder_by_column(spcg_ctx* c) {
   Sketch& s = c->sk;
@@ -577,10 +938,73 @@ static spcg_status householder_by_column(spcg_ctx* c) {
   return SPCG_OK;
 }
 
+static spcg_status finish_precond(spcg_ctx* c);
+
+// The look-ahead QR when it applies (more than one panel, an update group of
+// at least one CTA, the panel rows in shared memory); false: use k_qr_coop.
+static bool launch_qr_la(spcg_ctx* c, bool* launched) {
+  *launched = false;
+  Sketch& s = c->sk;
+  const int d = c->d;
+  const int64_t r = s.sched.r;
+  // with fewer than eight panels there is little to overlap: k_qr_coop
+  if (c->opts.qr_by_column != 0 || d < kQrLaMinD) return true;
+  const int G = qr_coop_grid(r, c->num_sms);
+  // panel group: about kQrLaPanelWork / d CTAs, at most half the grid (the
+  // panel path shortens with more CTAs, the trailing update with fewer;
+  // measured best near 63 at d = 500 and 24-37 at d = 1000, r = 6d)
+  int GP = c->opts.qr_panel_ctas > 0 ? c->opts.qr_panel_ctas : kQrLaPanelWork / d;
+  if (c->opts.qr_panel_ctas <= 0 && GP > G / 2) GP = G / 2;
+  if (GP > G - 1) GP = G - 1;
+  if (GP < 1) return true;
+  const int64_t chunk_max = (r + GP - 1) / GP;
+  const int64_t chunk_u = (r + (G - GP) - 1) / (G - GP);
+  const size_t smem = qr_la_smem(chunk_max, chunk_u);
+  if (smem > (size_t)200 * 1024) return true;
+  if (cudaFuncSetAttribute(k_qr_la, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return false;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_la, QT, smem) != cudaSuccess)
+    return false;
+  if (per_sm < 1) return true;
+  if (cudaMemsetAsync(s.qr_bar, 0, 3 * kBarWords * sizeof(unsigned), c->stream) != cudaSuccess)
+    return false;
+  QrLaArgs a{};
+  a.A = s.Ahat;
+  a.r = r;
+  a.d = d;
+  a.gp = GP;
+  a.chunk_max = (int)chunk_max;
+  a.Tg = s.qr_tg;
+  a.Rdiag = s.Rdiag;
+  a.vdiag = s.qr_vdiag;
+  a.red = s.qr_red;
+  a.Wl = s.qr_wl;
+  a.Wp = s.qr_wp;
+  a.Wt = s.qr_wt;
+  a.chunk_u = (int)chunk_u;
+  a.bar = s.qr_bar;
+  a.bar2 = s.qr_bar + kBarWords;
+  a.bar3 = s.qr_bar + 2 * kBarWords;
+  a.status = &c->scal->status;
+  a.spin = c->opts.spin_budget > 0 ? c->opts.spin_budget : (1ll << 31);
+  void* args[] = {&a};
+  if (cudaLaunchCooperativeKernel((const void*)k_qr_la, dim3(G), dim3(QT), args, smem,
+                                  c->stream) != cudaSuccess)
+    return false;
+  c->n_launch += 1;
+  *launched = true;
+  return true;
+}
+
 spcg_status launch_precond_factor(spcg_ctx* c) {
   Sketch& s = c->sk;
   const int d = c->d;
   const int64_t r = s.sched.r;
+  bool la = false;
+  if (!launch_qr_la(c, &la)) return SPCG_E_CUDA;
+  if (la) return finish_precond(c);
   int G = qr_coop_grid(r, c->num_sms);
   // the panels are factored by the first GP CTAs, about kQrPanelRows rows each:
   // fewer CTAs in each column step's reduction and barrier (latency), more rows
@@ -591,7 +1015,7 @@ spcg_status launch_precond_factor(spcg_ctx* c) {
   if (GP < 1) GP = 1;
   const int64_t chunk_max = (r + GP - 1) / GP;
   const size_t smem = qr_coop_smem(chunk_max);
-  bool coop = smem <= (size_t)200 * 1024 && c->opts.qr_by_column == 0;
+  bool coop = smem <= (size_t)200 * 1024 && c->opts.qr_by_column != 1;
   if (coop) {
     SPCG_CK(cudaFuncSetAttribute(k_qr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -623,6 +1047,14 @@ spcg_status launch_precond_factor(spcg_ctx* c) {
   } else {
     SPCG_TRY(householder_by_column(c));
   }
+  return finish_precond(c);
+}
+
+// R from the reduced sketch, R^{-1} and R^{-T}.
+static spcg_status finish_precond(spcg_ctx* c) {
+  Sketch& s = c->sk;
+  const int d = c->d;
+  const int64_t r = s.sched.r;
   const int64_t dd = (int64_t)d * d;
   int g = (int)((dd + 255) / 256);
   if (g > 4096) g = 4096;

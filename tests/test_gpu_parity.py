@@ -238,15 +238,17 @@ def test_transform_variants_and_plans_are_bit_identical():
     assert np.all(np.abs(Zg - Zo) <= _transform_tol(X, Y, n_pad, Zo))
 
 
-# Both factorisations of the preconditioner sketch: the blocked cooperative QR
-# (panels of 32 columns; widths below, at and just above one panel, ragged
-# last panels; panel groups of the default size, one CTA and five CTAs) and
-# the per-column steps, each against the oracle's R within
-# the Householder backward-error bound; a sketch of 120000 rows takes the
-# per-column path either way (its panel rows do not fit in shared memory).
+# The factorisations of the preconditioner sketch: the blocked cooperative QR
+# with look-ahead and without (panels of 32 columns; widths below, at and just
+# above one panel, ragged last panels, 16 panels; panel groups of the default
+# size, one CTA and five CTAs) and the per-column steps, each against the
+# oracle's R within the Householder backward-error bound; a sketch of 120000
+# rows takes the per-column path either way (its panel rows do not fit in
+# shared memory).
 @pytest.mark.parametrize("N,d,r,seed", [(20000, 50, None, 1), (4000, 32, None, 2), (4000, 33, None, 3),
                                         (9000, 300, None, 4), (70000, 129, None, 8),
-                                        (3000, 7, None, 6), (1 << 17, 8, 120000, 5)])
+                                        (3000, 7, None, 6), (1 << 17, 8, 120000, 5),
+                                        (20000, 500, None, 9)])
 def test_qr_blocked_and_per_column_agree(N, d, r, seed):
     X, Y, _ = gaussian_problem(N, d, 1.0, seed=seed)
     sched = OS.default_schedule(N, d)
@@ -259,8 +261,9 @@ def test_qr_blocked_and_per_column_agree(N, d, r, seed):
     kappa = np.linalg.cond(A_hat)
     tol_R = 2 * math.sqrt(2) * kappa * gamma(r * d) * (np.linalg.norm(A_hat) / np.linalg.norm(A_hat, 2))
     Rs = []
-    # blocked QR (automatic panel group, one panel CTA, five), then per column
-    for by_col, panel_ctas in ((0, 0), (0, 1), (0, 5), (1, 0)):
+    # blocked QR with look-ahead (automatic panel group, one panel CTA, five),
+    # per column, blocked without look-ahead (automatic, five)
+    for by_col, panel_ctas in ((0, 0), (0, 1), (0, 5), (1, 0), (2, 0), (2, 5)):
         o = S.Opts()
         o.qr_by_column = by_col
         o.qr_panel_ctas = panel_ctas
