@@ -285,6 +285,10 @@ def run_batched(args, w):
     ms_b = float(np.median(times))
     betas = [b.clone() for b in B.betas]
     phases = batch_phase_summary(B, Xs)
+    peak_gbs, peak_src = hbm_peak()
+    bound = batch_streaming_bound(shapes, it, peak_gbs)
+    bound["x_bound"] = ms_b / bound["bound_ms"]
+    bound["peak_source"] = peak_src
     B.close()
     # the comparator: one plain FP64 spcg_solve per problem, back to back
     loop_ms = 0.0
@@ -319,14 +323,42 @@ def run_batched(args, w):
                         "max_rel_pred_error": float(max(errs)),
                         "problems_meeting_tol": int(sum(1 for e in errs if e <= w["tol"])),
                         "autotuned_chunk_bytes": tiles,
-                        "x_bytes_fp32": int(total_bytes), "phase_ms": phases},
+                        "x_bytes_fp32": int(total_bytes), "phase_ms": phases,
+                        "streaming_bound": bound},
             "loop_plain_fp64": {"s": loop_ms / 1e3,
                                 "status_ok": int(sum(1 for v in loop_status if v == 0))},
             "speedup_batched_vs_loop": loop_ms / ms_b if ms_b > 0 else None,
             "accuracy_reference": "torch.linalg.lstsq (FP64, QR) of each problem's FP32 values"}
 
 
-PHASES = ("colmax", "countsketch", "stage_matrices", "qr", "stage1", "stage2")
+PHASES = ("colmax", "cs_maps", "cs_sums", "stage_matrices", "qr", "stage1", "stage2")
+
+
+def batch_streaming_bound(shapes, iters, peak_gbs):
+    """Algorithmic bytes of one batched solve and the time they take at the
+    measured HBM bandwidth.  Per problem (N x d FP32, C = d + 1 with Y, the
+    default stages m_i = 2^ceil(log2 8d) doubling to N'/2, a_i = 3, r = 6d):
+    the column maxima and the CountSketch each read [X Y] once; the sketch
+    writes its m_K int64 bucket rows and the r FP32 preconditioner rows; the
+    stage matrices are written once as FP32 and read a_i + 1 times by Stage I
+    (a residual pass and a_i iterations); Stage II reads X once per
+    iteration plus two true gradients (its start and the confirmed stop)."""
+    total = 0
+    for (N, d), it in zip(shapes, iters):
+        C, ld = d + 1, (d + 3) // 4 * 4
+        n_pad = 1 << (N - 1).bit_length()
+        m, mi = [], 1 << (8 * d - 1).bit_length()
+        while mi <= n_pad // 2:
+            m.append(mi)
+            mi *= 2
+        xb = N * C * 4
+        b = 2 * xb                                    # column maxima, CountSketch read
+        b += (m[-1] * C * 8 if m else 0) + 6 * d * d * 4   # bucket rows, preconditioner rows
+        b += sum(mi * ld * 4 * (1 + 3 + 1) for mi in m)    # stage matrices: write, 4 reads
+        b += (int(it) + 2) * N * d * 4                # Stage II passes and true gradients
+        total += b
+    return {"alg_bytes": int(total), "peak_gbs": peak_gbs,
+            "bound_ms": total / (peak_gbs * 1e6)}
 
 
 def batch_phase_summary(B, Xs, sm_mhz=2032.0):

@@ -524,10 +524,11 @@ spcg_status spcg_solve_batched(const spcg_problem_f32* probs, int32_t n, uint64_
                                int32_t* iters_out);
 
 /* Clock cycles (of the SM that solved it) spent by each problem of the last
- * spcg_batch_solve in its phases: [0] column maxima, [1] CountSketch buckets,
- * [2] stage matrices, [3] preconditioner QR and R^{-1}, [4] Stage I, [5] Stage
- * II; [6], [7] zero.  cycles_out: host, 8 n int64 in the order of the problems
- * given to spcg_batch_create. */
+ * spcg_batch_solve in its phases: [0] column maxima, [1] CountSketch row maps
+ * (bucket sizes, offsets, row lists), [2] CountSketch bucket sums, [3] stage
+ * matrices, [4] preconditioner QR and R^{-1}, [5] Stage I, [6] Stage II; [7]
+ * zero.  cycles_out: host, 8 n int64 in the order of the problems given to
+ * spcg_batch_create. */
 spcg_status spcg_batch_phase_cycles(spcg_batch* b, int64_t* cycles_out);
 
 /* Rows per streamed chunk, as chunk bytes per width class (d <= 32, <= 64,

@@ -34,6 +34,7 @@ constexpr int B_STAGES = 6;
 constexpr int B_MAXD = 256;
 constexpr int B_NI = B_MAXD / 32;         // columns per lane
 constexpr int B_RU = 4;                   // rows (or elements) a thread loads at once outside the ring
+constexpr int B_SR = 4;                   // rows of a stage bucket loaded at once (lane per bucket)
 
 struct BatchProblemDev {
   const float* X;
@@ -434,6 +435,8 @@ __device__ void precond(const float* Rinv, const float* RinvT, int d, const doub
 }
 
 constexpr size_t B_RING = (size_t)B_STAGES * 16384;
+static_assert((size_t)6 * B_MAXD * sizeof(float) <= B_RING,
+              "the QR stages a reflector of r = 6d <= 1536 rows in the ring");
 constexpr size_t B_SMEM = B_RING + ((sizeof(BShared) + 127) & ~(size_t)127) + 128;
 
 __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
@@ -581,49 +584,105 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
       rlist[slot] = (int32_t)((uint32_t)j | ((wh.y & 1u) << 31));
     }
     __syncthreads();
-    // bucket sums: a warp per bucket, lanes over the columns of each row, the
-    // loads of B_RU rows of the bucket issued before their sums
-    for (int64_t t = warp; t < nb; t += nw) {
-      const bool hat = t >= mK;
-      long long acc[(B_MAXD + 1 + 31) / 32];
+    phase_mark(1);
+    // bucket sums.  Stage buckets (about two rows each, N'/2 of them): a lane
+    // per bucket, columns in chunks of 8 (two 16-byte loads per row), the
+    // first B_SR rows' loads of a chunk issued before their sums, so that a
+    // CTA keeps hundreds of buckets' rows in flight.  Preconditioner buckets
+    // (N / r rows each): a warp per bucket, lanes over the columns, the loads
+    // of B_RU rows issued before their sums.
+    {
+      constexpr int CCH = 8;
+      for (int64_t tb = (int64_t)warp * 32; tb < mK; tb += (int64_t)nw * 32) {
+        const int64_t t = tb + lane;
+        const bool live = t < mK;
+        const int k0 = live ? cnt[t] : 0, k1 = live ? cur[t] : 0;
+        uint32_t ent[B_SR];
 #pragma unroll
-      for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) acc[u] = 0;
-      const int k1 = cur[t];
-      for (int k0 = cnt[t]; k0 < k1; k0 += B_RU) {
-        float v[B_RU][(B_MAXD + 1 + 31) / 32];
-        uint32_t ent[B_RU];
+        for (int q = 0; q < B_SR; ++q) ent[q] = k0 + q < k1 ? (uint32_t)rlist[k0 + q] : 0u;
+        for (int c0 = 0; c0 < C; c0 += CCH) {
+          long long acc[CCH];
 #pragma unroll
-        for (int q = 0; q < B_RU; ++q) ent[q] = k0 + q < k1 ? (uint32_t)rlist[k0 + q] : 0u;
+          for (int u = 0; u < CCH; ++u) acc[u] = 0;
+          const bool vec = c0 + CCH <= d;   // eight columns of X, 16-byte aligned
+          for (int kb = k0; kb < k1; kb += B_SR) {
+            float v[B_SR][CCH];
 #pragma unroll
-        for (int q = 0; q < B_RU; ++q) {
-          const int64_t j = ent[q] & 0x7FFFFFFFu;
+            for (int q = 0; q < B_SR; ++q) {
+              const uint32_t e = kb == k0 ? ent[q] : (kb + q < k1 ? (uint32_t)rlist[kb + q] : 0u);
+              const int64_t j = e & 0x7FFFFFFFu;   // rows past the bucket read row 0
+              if (vec) {
+                const float4 a4 = *reinterpret_cast<const float4*>(P.X + j * ldx + c0);
+                const float4 b4 = *reinterpret_cast<const float4*>(P.X + j * ldx + c0 + 4);
+                v[q][0] = a4.x; v[q][1] = a4.y; v[q][2] = a4.z; v[q][3] = a4.w;
+                v[q][4] = b4.x; v[q][5] = b4.y; v[q][6] = b4.z; v[q][7] = b4.w;
+              } else {
 #pragma unroll
-          for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
-            const int c = lane + 32 * u;
-            v[q][u] = (c < C && k0 + q < k1) ? ((c < d) ? P.X[j * ldx + c] : P.Y[j]) : 0.f;
-          }
-        }
+                for (int u = 0; u < CCH; ++u) {
+                  const int c = c0 + u;
+                  v[q][u] = c < d ? P.X[j * ldx + c] : (c == d ? P.Y[j] : 0.f);
+                }
+              }
+            }
 #pragma unroll
-        for (int q = 0; q < B_RU; ++q)
+            for (int q = 0; q < B_SR; ++q) {
+              if (kb + q >= k1) break;
+              const uint32_t e = kb == k0 ? ent[q] : (uint32_t)rlist[kb + q];
 #pragma unroll
-          for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
-            const int c = lane + 32 * u;
-            if (c < C) {
-              const long long fq = fixed_from_f32(v[q][u], sh.colshift[c]);
-              acc[u] += (ent[q] >> 31) ? -fq : fq;   // rows past the bucket hold 0
+              for (int u = 0; u < CCH; ++u) {
+                const int c = c0 + u;
+                if (c < C) {
+                  const long long fq = fixed_from_f32(v[q][u], sh.colshift[c]);
+                  acc[u] += (e >> 31) ? -fq : fq;
+                }
+              }
             }
           }
-      }
+          if (live)
 #pragma unroll
-      for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
-        const int c = lane + 32 * u;
-        if (c >= C) continue;
-        if (!hat) buckets[t * C + c] = acc[u];
-        else if (c < d) Ahat[(int64_t)c * r + (t - mK)] = f32_from_fixed(acc[u], sh.colshift[c]);
+            for (int u = 0; u < CCH; ++u)
+              if (c0 + u < C) buckets[t * C + c0 + u] = acc[u];
+        }
+      }
+      for (int64_t t = mK + warp; t < nb; t += nw) {
+        long long acc[(B_MAXD + 1 + 31) / 32];
+#pragma unroll
+        for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) acc[u] = 0;
+        const int k1 = cur[t];
+        for (int k0 = cnt[t]; k0 < k1; k0 += B_RU) {
+          float v[B_RU][(B_MAXD + 1 + 31) / 32];
+          uint32_t ent[B_RU];
+#pragma unroll
+          for (int q = 0; q < B_RU; ++q) ent[q] = k0 + q < k1 ? (uint32_t)rlist[k0 + q] : 0u;
+#pragma unroll
+          for (int q = 0; q < B_RU; ++q) {
+            const int64_t j = ent[q] & 0x7FFFFFFFu;
+#pragma unroll
+            for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
+              const int c = lane + 32 * u;
+              v[q][u] = (c < C && k0 + q < k1) ? ((c < d) ? P.X[j * ldx + c] : P.Y[j]) : 0.f;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < B_RU; ++q)
+#pragma unroll
+            for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
+              const int c = lane + 32 * u;
+              if (c < C) {
+                const long long fq = fixed_from_f32(v[q][u], sh.colshift[c]);
+                acc[u] += (ent[q] >> 31) ? -fq : fq;   // rows past the bucket hold 0
+              }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < (B_MAXD + 1 + 31) / 32; ++u) {
+          const int c = lane + 32 * u;
+          if (c < d) Ahat[(int64_t)c * r + (t - mK)] = f32_from_fixed(acc[u], sh.colshift[c]);
+        }
       }
     }
     __syncthreads();
-    phase_mark(1);
+    phase_mark(2);
     // 3. stage matrices by folding the buckets modulo m_i (integer adds)
     int64_t off[SPCG_MAX_STAGES];
     {
@@ -656,37 +715,37 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
       }
       float* S_i = stages + off[i] * ld;
       double* b_i = bst + off[i];
-      const int64_t ne = cur_m * ld;
-      for (int64_t e0 = tid; e0 < ne; e0 += (int64_t)blockDim.x * B_RU) {
-        long long qv[B_RU];
+      // a warp per stage row, lanes over its columns (no index division)
+      for (int64_t t = warp; t < cur_m; t += nw) {
+        const long long* src = buckets + t * C;
+        float* dst = S_i + t * ld;
+        long long qv[(B_MAXD + 4 + 31) / 32];
 #pragma unroll
-        for (int q = 0; q < B_RU; ++q) {
-          const int64_t e = e0 + (int64_t)q * blockDim.x;
-          const int64_t t = e / ld;
-          const int c = (int)(e % ld);
-          qv[q] = (e < ne && c < d) ? buckets[t * C + c] : 0;
+        for (int u = 0; u < (B_MAXD + 4 + 31) / 32; ++u) {
+          const int c = lane + 32 * u;
+          qv[u] = c < d ? src[c] : 0;
         }
 #pragma unroll
-        for (int q = 0; q < B_RU; ++q) {
-          const int64_t e = e0 + (int64_t)q * blockDim.x;
-          if (e >= ne) continue;
-          const int64_t t = e / ld;
-          const int c = (int)(e % ld);
-          S_i[e] = (c < d) ? f32_from_fixed(qv[q], sh.colshift[c]) : 0.f;
-          if (c == 0) b_i[t] = f64_from_fixed(buckets[t * C + d], sh.colshift[d]);
+        for (int u = 0; u < (B_MAXD + 4 + 31) / 32; ++u) {
+          const int c = lane + 32 * u;
+          if (c < ld) dst[c] = c < d ? f32_from_fixed(qv[u], sh.colshift[c]) : 0.f;
         }
+        if (lane == 0) b_i[t] = f64_from_fixed(src[d], sh.colshift[d]);
       }
       __syncthreads();
     }
     __syncthreads();
-    phase_mark(2);
+    phase_mark(3);
     // 4. Householder QR of S-hat X (FP32), R with positive diagonal, R^{-1}
+    float* vk = reinterpret_cast<float*>(ring);   // x(k : r) of step k (the ring is idle here)
     for (int k = 0; k < d; ++k) {
-      float* colk = Ahat + (int64_t)k * r;
+      const float* colk = Ahat + (int64_t)k * r;
+      for (int64_t i = k + tid; i < r; i += blockDim.x) vk[i] = colk[i];
+      __syncthreads();
       double s2 = 0.0;
-      for (int64_t i = k + 1 + tid; i < r; i += blockDim.x) s2 += (double)colk[i] * colk[i];
+      for (int64_t i = k + 1 + tid; i < r; i += blockDim.x) s2 += (double)vk[i] * vk[i];
       s2 = bsum(s2, tmp);
-      const double x0 = colk[k];
+      const double x0 = vk[k];
       const double normx = sqrt(x0 * x0 + s2);
       const double alpha = (x0 >= 0.0) ? -normx : normx;
       const double v0 = x0 - alpha;
@@ -696,28 +755,34 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
         const float tau = (float)(2.0 / vv), v0f = (float)v0;
         for (int j = k + 1 + warp; j < d; j += nw) {
           float* cj = Ahat + (int64_t)j * r;
-          // four independent partial sums: four pairs of loads in flight
-          float s0 = 0.f, s1 = 0.f, s2f = 0.f, s3 = 0.f;
+          // eight independent partial sums: eight loads of the column in
+          // flight, the reflector from shared memory
+          float sp[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) sp[u] = 0.f;
           int64_t i = k + 1 + lane;
-          for (; i + 96 < r; i += 128) {
-            s0 = fmaf(colk[i], cj[i], s0);
-            s1 = fmaf(colk[i + 32], cj[i + 32], s1);
-            s2f = fmaf(colk[i + 64], cj[i + 64], s2f);
-            s3 = fmaf(colk[i + 96], cj[i + 96], s3);
+          for (; i + 224 < r; i += 256) {
+            float cv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) cv[u] = cj[i + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sp[u] = fmaf(vk[i + 32 * u], cv[u], sp[u]);
           }
-          for (; i < r; i += 32) s0 = fmaf(colk[i], cj[i], s0);
-          float sd = warp_allsum((s0 + s1) + (s2f + s3)) + v0f * cj[k];
+          for (; i < r; i += 32) sp[0] = fmaf(vk[i], cj[i], sp[0]);
+          const float sd =
+              warp_allsum(((sp[0] + sp[1]) + (sp[2] + sp[3])) + ((sp[4] + sp[5]) + (sp[6] + sp[7]))) +
+              v0f * cj[k];
           const float f = tau * sd;
           if (lane == 0) cj[k] -= f * v0f;
           i = k + 1 + lane;
-          for (; i + 96 < r; i += 128) {
-            const float c0 = cj[i], c1 = cj[i + 32], c2 = cj[i + 64], c3 = cj[i + 96];
-            cj[i] = fmaf(-f, colk[i], c0);
-            cj[i + 32] = fmaf(-f, colk[i + 32], c1);
-            cj[i + 64] = fmaf(-f, colk[i + 64], c2);
-            cj[i + 96] = fmaf(-f, colk[i + 96], c3);
+          for (; i + 224 < r; i += 256) {
+            float cv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) cv[u] = cj[i + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) cj[i + 32 * u] = fmaf(-f, vk[i + 32 * u], cv[u]);
           }
-          for (; i < r; i += 32) cj[i] = fmaf(-f, colk[i], cj[i]);
+          for (; i < r; i += 32) cj[i] = fmaf(-f, vk[i], cj[i]);
         }
       }
       __syncthreads();
@@ -762,7 +827,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
       }
       __syncthreads();
     }
-    phase_mark(3);
+    phase_mark(4);
     double* beta = sh.dvec[0];
     double* g = sh.dvec[1];
     double* z = sh.dvec[2];
@@ -840,7 +905,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
           break;
         }
     }
-    phase_mark(4);
+    phase_mark(5);
     // 6. Stage II with the stopping rule confirmed on true gradients
     int total = 0, restarts = 0, converged = 0;
     const double tau = a.tol / 2.0;
@@ -873,7 +938,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
       ++restarts;
     }
     if (status == 0 && !converged) status = 5;
-    phase_mark(5);
+    phase_mark(6);
     for (int c = tid; c < d; c += blockDim.x) P.beta[c] = beta[c];
     if (tid == 0) {
       *P.status = status;

@@ -653,10 +653,11 @@ class Batch:
 
     def phase_cycles(self):
         """Per problem, the SM clock cycles of each phase of the last solve
-        (column maxima, CountSketch, stage matrices, QR, Stage I, Stage II)."""
+        (column maxima, CountSketch row maps, CountSketch sums, stage
+        matrices, QR, Stage I, Stage II)."""
         arr = (ctypes.c_int64 * (8 * self.n))()
         _check(lib().spcg_batch_phase_cycles(self.h, arr), "spcg_batch_phase_cycles")
-        return [list(arr[8 * i: 8 * i + 6]) for i in range(self.n)]
+        return [list(arr[8 * i: 8 * i + 7]) for i in range(self.n)]
 
     def set_tiles(self, chunk_bytes4):
         arr = (ctypes.c_int32 * 4)(*chunk_bytes4)
