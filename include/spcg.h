@@ -453,9 +453,8 @@ spcg_status spcg_split_f32(const double* X, int64_t N, int32_t d, int64_t ldx, f
  * partial sums for up to 160 CTAs x 1024 columns plus a status word), held by
  * every GPU that loads the library until the process exits.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current, so make the first call on each device outside any stream
- * capture.  All calls share the array: calls that overlap on the GPU race and
- * may return wrong results.
+ * device current; a failed lookup is retried by the next call.  All calls share
+ * the array: calls that overlap on the GPU race and may return wrong results.
  * Errors: SPCG_E_INVALID_ARG, SPCG_E_CUDA, SPCG_E_TIMEOUT.
  */
 spcg_status spcg_gram_apply_noalloc(const double* A, int64_t m, int32_t d, int64_t lda,
