@@ -10,8 +10,8 @@
 // use the array's name as a device address: on the host it names a shadow
 // object.  The address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, by the first call on that
-// device; that first call should therefore come before any stream capture.
-// A failed lookup is not remembered: the next call on that device tries again.
+// device.  A failed lookup is not remembered: the next call on that device
+// tries again.
 //
 // All calls share the array and it keeps the last call's contents: the
 // status word is cleared on the caller's stream before each launch, and the
