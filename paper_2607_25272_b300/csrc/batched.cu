@@ -35,6 +35,7 @@ constexpr int B_MAXD = 256;
 constexpr int B_NI = B_MAXD / 32;         // columns per lane
 constexpr int B_RU = 4;                   // rows (or elements) a thread loads at once outside the ring
 constexpr int B_SR = 4;                   // rows of a stage bucket loaded at once (lane per bucket)
+constexpr int B_CCH = 8;                  // columns per chunk of a stage bucket (lane per bucket)
 
 struct BatchProblemDev {
   const float* X;
@@ -592,7 +593,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
     // (N / r rows each): a warp per bucket, lanes over the columns, the loads
     // of B_RU rows issued before their sums.
     {
-      constexpr int CCH = 8;
+      constexpr int CCH = B_CCH;
       for (int64_t tb = (int64_t)warp * 32; tb < mK; tb += (int64_t)nw * 32) {
         const int64_t t = tb + lane;
         const bool live = t < mK;
@@ -612,10 +613,14 @@ __global__ void __launch_bounds__(BT, 1) k_batched_spcg(const BatchArgs a) {
               const uint32_t e = kb == k0 ? ent[q] : (kb + q < k1 ? (uint32_t)rlist[kb + q] : 0u);
               const int64_t j = e & 0x7FFFFFFFu;   // rows past the bucket read row 0
               if (vec) {
-                const float4 a4 = *reinterpret_cast<const float4*>(P.X + j * ldx + c0);
-                const float4 b4 = *reinterpret_cast<const float4*>(P.X + j * ldx + c0 + 4);
-                v[q][0] = a4.x; v[q][1] = a4.y; v[q][2] = a4.z; v[q][3] = a4.w;
-                v[q][4] = b4.x; v[q][5] = b4.y; v[q][6] = b4.z; v[q][7] = b4.w;
+#pragma unroll
+                for (int h = 0; h < CCH / 4; ++h) {
+                  const float4 a4 = *reinterpret_cast<const float4*>(P.X + j * ldx + c0 + 4 * h);
+                  v[q][4 * h] = a4.x;
+                  v[q][4 * h + 1] = a4.y;
+                  v[q][4 * h + 2] = a4.z;
+                  v[q][4 * h + 3] = a4.w;
+                }
               } else {
 #pragma unroll
                 for (int u = 0; u < CCH; ++u) {
