@@ -81,14 +81,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-constexpr int kConsumers = 12;                // consumer warps of k_pass (upper bound)
+constexpr int kConsumers = 12;                // consumer warps of the FP64 and FP32 passes
+constexpr int kMaxConsumers = 15;             // the most any pass uses (scratch sizing)
 // Consumer warps per CTA: fewer for the widest rows, whose accumulators need
-// the registers.
+// the registers; BF16 rows, and FP32 rows up to 512 columns, take 15 (more
+// warps hide the latency of short rows: BF16 10-17 % faster than with 12 at
+// 128-1000 columns, FP32 13-15 % at 128-256 columns).
 // (Registers come in blocks of four warps: 13 warps get no more registers
 // than 16 would, 12 warps get as many as 12.)
 template <int NI, int ES = 8>   // ES: element size of the operand
 struct PassCfg {
-  static constexpr int C = NI < 32 ? kConsumers : (ES == 8 ? 8 : (ES == 4 ? 11 : kConsumers));
+  static constexpr int C = ES == 2 ? kMaxConsumers
+                          : (NI < 32 ? (ES == 4 ? kMaxConsumers : kConsumers) : (ES == 8 ? 8 : 11));
   static constexpr int THREADS = 32 * (C + 1);
 };
 constexpr int kMaxStages = 8;
@@ -771,7 +775,7 @@ spcg_status make_pass_geom_t(const void* A, int64_t m, int d, int64_t lda, int d
   g->stage_bytes = stage;
   const size_t ni32 = (size_t)ni_for(d) * 32;
   const size_t cover = ni32 > 256 ? ni32 : 256;   // columns a consumer warp covers
-  size_t red = (size_t)kConsumers * cover * 8;
+  size_t red = (size_t)kMaxConsumers * cover * 8;
   size_t tiles = stage * stages;
   if (tiles < red) tiles = red;
   g->region_bytes = tiles;
