@@ -31,3 +31,20 @@ def test_phase_groups_cover_every_phase_once():
             ph = list(range(n_phases))
             groups = bench.phase_groups(ph, K)
             assert sum(groups, []) == ph and len(groups) == K
+
+
+def test_batched_streaming_bound_counts_every_phase():
+    """The batch's streaming bound for one problem, counted by hand: N = 5000,
+    d = 20 (C = 21, ld = 20, N' = 8192, stages 256, 512, ..., 4096, r = 120)
+    and 7 Stage II iterations."""
+    import bench
+    N, d, it = 5000, 20, 7
+    C, ld = 21, 20
+    m = [256, 512, 1024, 2048, 4096]
+    want = 2 * N * C * 4                       # column maxima, CountSketch read
+    want += 4096 * C * 8 + 6 * d * d * 4       # S_K bucket rows, preconditioner rows
+    want += sum(mi * ld * 4 * 5 for mi in m)   # stage matrices written once, read 4 times
+    want += (it + 2) * N * d * 4               # Stage II passes and two true gradients
+    b = bench.batch_streaming_bound([(N, d)], [it], 1000.0)
+    assert b["alg_bytes"] == want
+    assert abs(b["bound_ms"] - want / 1e9) < 1e-12
