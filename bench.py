@@ -59,6 +59,10 @@ NOMINAL_FP64_TFLOPS = 1.25    # B300 FP64, nominal (context only)
 # 2.704384 MB for 1.048576 GB of rows.  Set to None whenever the kernel changes
 # after the capture.
 K_PASS_TRAFFIC_RATIO = (1.048634624e9 + 2.704384e6) / 1.048576e9
+# The same for k_pass_df (the double-FP32 pair) on rows of 1000 columns, from
+# the ncu capture of this kernel on a 262144 x 1000 pair: read 2.097235 GB +
+# wrote 3.191808 MB for 2.097152 GB of Xh and Xl.  None once the kernel changes.
+K_PASS_DF_TRAFFIC_RATIO = (2.097235e9 + 3.191808e6) / 2.097152e9
 
 
 def make_problem(w, N=None, seed_offset=0):
@@ -201,10 +205,11 @@ def run_forms(args, w):
                      "grad_prec": info.grad_prec, "launches": info.launches,
                      "passes_by_operand": by_op}
         if name == "mixed":
+            df = info.inner_prec == S.INNER_DF
             res[name]["roofline"] = pass_roofline(
-                pinfo, "pair" if info.inner_prec == S.INNER_DF else "float32", peak, peak_src,
-                None, "k_pass_df (double-FP32 pair)" if info.inner_prec == S.INNER_DF
-                else "k_pass<float>")
+                pinfo, "pair" if df else "float32", peak, peak_src,
+                K_PASS_DF_TRAFFIC_RATIO if (df and d == 1000) else None,
+                "k_pass_df (double-FP32 pair)" if df else "k_pass<float>")
     # end to end through the public API from pinned host buffers, when the
     # host can hold a pinned copy of X (33.6 GB)
     e2e = None
