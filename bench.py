@@ -63,6 +63,10 @@ K_PASS_TRAFFIC_RATIO = (1.048634624e9 + 2.704384e6) / 1.048576e9
 # the ncu capture of this kernel on a 262144 x 1000 pair: read 2.097235 GB +
 # wrote 3.191808 MB for 2.097152 GB of Xh and Xl.  None once the kernel changes.
 K_PASS_DF_TRAFFIC_RATIO = (2.097235e9 + 3.191808e6) / 2.097152e9
+# And for k_pass<float> (the FP32 copy of X) on rows of 500 columns, from the
+# ncu capture on a 262144 x 500 FP32 operand: read 524.349184 MB + wrote
+# 2.655232 MB for 524.288 MB of rows.  None once the kernel changes.
+K_PASS_F32_TRAFFIC_RATIO = (524349184 + 2655232) / 524288000
 
 
 def make_problem(w, N=None, seed_offset=0):
@@ -208,7 +212,8 @@ def run_forms(args, w):
             df = info.inner_prec == S.INNER_DF
             res[name]["roofline"] = pass_roofline(
                 pinfo, "pair" if df else "float32", peak, peak_src,
-                K_PASS_DF_TRAFFIC_RATIO if (df and d == 1000) else None,
+                K_PASS_DF_TRAFFIC_RATIO if (df and d == 1000)
+                else (K_PASS_F32_TRAFFIC_RATIO if (not df and d == 500) else None),
                 "k_pass_df (double-FP32 pair)" if df else "k_pass<float>")
     # end to end through the public API from pinned host buffers, when the
     # host can hold a pinned copy of X (33.6 GB)
@@ -937,7 +942,8 @@ def run_ours(args, w, rank, world, local_rank):
                       "refine_iters": minfos[-1].refine_iters, "restarts": minfos[-1].restarts,
                       "cond_est": minfos[-1].cond_est, "inner_prec": minfos[-1].inner_prec,
                       "grad_prec": minfos[-1].grad_prec,
-                      "roofline": pass_roofline(mpinfo, "float32", hbm_peak_gbs, hbm_src, None,
+                      "roofline": pass_roofline(mpinfo, "float32", hbm_peak_gbs, hbm_src,
+                                                K_PASS_F32_TRAFFIC_RATIO if w["d"] == 500 else None,
                                                 "k_pass<float> (Stage II on the FP32 copy)")}},
         "gpu_launches": launches,
         "roofline": roofline,
