@@ -193,6 +193,8 @@ constexpr int QT = 256;                // threads per CTA
 constexpr int QLD = QB + 1;            // row stride of the panel slice in shared memory
 constexpr int QCOLB = 8;               // columns per batch in the T^T W phase
 constexpr int QUNR = 8;                // independent loads in flight per thread in the sums
+constexpr int QRED = 16;               // the same in a column step's read-back (one round for
+                                       // up to 64 panel CTAs)
 constexpr int kQrPanelRows = 48;       // rows per panel CTA (default panel group size)
 constexpr int QRR = 4;                 // rows per step of the trailing-update loops
 constexpr int kQrLaPanelWork = 30000;  // look-ahead QR: panel CTAs = this / d (default)
@@ -280,15 +282,15 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
           // then the four quarter sums in order
           const int sl = tid % QSL, grp = tid / QSL;
           double acc = 0.0;
-          for (int g0 = grp; g0 < GP; g0 += 4 * QUNR) {   // loads first, then the sums in order
-            double v[QUNR];
+          for (int g0 = grp; g0 < GP; g0 += 4 * QRED) {   // loads first, then the sums in order
+            double v[QRED];
 #pragma unroll
-            for (int k = 0; k < QUNR; ++k) {
+            for (int k = 0; k < QRED; ++k) {
               const int g = g0 + 4 * k;
               v[k] = g < GP ? red[(size_t)g * QSL + sl] : 0.0;
             }
 #pragma unroll
-            for (int k = 0; k < QUNR; ++k) acc += v[k];
+            for (int k = 0; k < QRED; ++k) acc += v[k];
           }
           comb[grp * QSL + sl] = acc;
         }
@@ -313,10 +315,16 @@ __global__ void __launch_bounds__(QT, 1) k_qr_coop(const QrCoopArgs a) {
         const double v0 = sc[0], tau = sc[1];
         // T(0:j, j) = -tau T(0:j, 0:j) V(:, 0:j)^T v_j, with
         // v_l^T v_j = (below the diagonal) + v_l(diag) v_0
-        if (tid < j) {
-          double sacc = 0.0;
-          for (int l = tid; l < j; ++l) sacc = fma(T[tid * QB + l], fma(tot[QB + l], v0, tot[l]), sacc);
-          T[tid * QB + j] = -tau * sacc;
+        if (tid < j) {   // four independent partial sums over l
+          double s4[4] = {0.0, 0.0, 0.0, 0.0};
+          int l = tid;
+          for (; l + 3 < j; l += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              s4[u] = fma(T[tid * QB + l + u], fma(tot[QB + l + u], v0, tot[l + u]), s4[u]);
+          }
+          for (; l < j; ++l) s4[0] = fma(T[tid * QB + l], fma(tot[QB + l], v0, tot[l]), s4[0]);
+          T[tid * QB + j] = -tau * ((s4[0] + s4[1]) + (s4[2] + s4[3]));
         } else if (tid == j) {
           T[j * QB + j] = tau;
         }
@@ -635,15 +643,15 @@ __global__ void __launch_bounds__(QT, 1) k_qr_la(const QrLaArgs a) {
         {
           const int sl = tid % QSL, grp = tid / QSL;
           double acc = 0.0;
-          for (int g0 = grp; g0 < GP; g0 += 4 * QUNR) {
-            double v[QUNR];
+          for (int g0 = grp; g0 < GP; g0 += 4 * QRED) {
+            double v[QRED];
 #pragma unroll
-            for (int k = 0; k < QUNR; ++k) {
+            for (int k = 0; k < QRED; ++k) {
               const int g = g0 + 4 * k;
               v[k] = g < GP ? red[(size_t)g * QSL + sl] : 0.0;
             }
 #pragma unroll
-            for (int k = 0; k < QUNR; ++k) acc += v[k];
+            for (int k = 0; k < QRED; ++k) acc += v[k];
           }
           comb[grp * QSL + sl] = acc;
         }
@@ -666,10 +674,16 @@ __global__ void __launch_bounds__(QT, 1) k_qr_la(const QrLaArgs a) {
         }
         __syncthreads();
         const double v0 = sc[0], tau = sc[1];
-        if (tid < j) {
-          double sacc = 0.0;
-          for (int l = tid; l < j; ++l) sacc = fma(T[tid * QB + l], fma(tot[QB + l], v0, tot[l]), sacc);
-          T[tid * QB + j] = -tau * sacc;
+        if (tid < j) {   // four independent partial sums over l
+          double s4[4] = {0.0, 0.0, 0.0, 0.0};
+          int l = tid;
+          for (; l + 3 < j; l += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              s4[u] = fma(T[tid * QB + l + u], fma(tot[QB + l + u], v0, tot[l + u]), s4[u]);
+          }
+          for (; l < j; ++l) s4[0] = fma(T[tid * QB + l], fma(tot[QB + l], v0, tot[l]), s4[0]);
+          T[tid * QB + j] = -tau * ((s4[0] + s4[1]) + (s4[2] + s4[3]));
         } else if (tid == j) {
           T[j * QB + j] = tau;
         }
