@@ -137,7 +137,9 @@ typedef struct {
                                per SM (9 or 10 levels; others as 1), 3 = the
                                per-round pass kernel; all give the same bits  */
   int32_t fwht_first_levels; /* levels of the first of two transform passes;
-                               0 = split evenly                               */
+                               0 = split evenly, except that the last pass
+                               gets 9 levels where the first then has at
+                               most 11 (N' = 2^20: 11 + 9)                    */
   int32_t qr_panel_ctas;    /* CTAs that factor each 32-column panel of the
                                preconditioner QR; 0 = about 30000 / d, at most
                                half the grid (with look-ahead), or one per 48

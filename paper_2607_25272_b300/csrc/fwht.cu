@@ -151,7 +151,7 @@ struct FwhtShape {
   static constexpr int TC = (L <= 1024) ? 16 : (L == 2048 ? 8 : 4);
   static constexpr int THREADS = 512;
   static constexpr int ROUNDS = (LOGL + 3) / 4;
-  static constexpr size_t SMEM = (size_t)L * TC * 8 + (size_t)L * 3 * 4 + (size_t)TC * 4;
+  static constexpr size_t SMEM = (size_t)L * TC * 8 + (size_t)L * 3 * 4;
 };
 
 // g-level butterfly on 2^g registers (index bits 0..g-1 of the register index).
@@ -169,88 +169,114 @@ __device__ __forceinline__ void bfly(long long (&v)[1 << G]) {
   }
 }
 
+// Register rounds of a LOGL-level pass: R rounds of g(rnd) levels (g <= 4),
+// round rnd starting at tile-row bit lev(rnd).  All compile-time, so every
+// shared-memory offset of a round is an immediate.
 template <int LOGL>
-__device__ __forceinline__ int round_levels(int rnd) {
-  constexpr int R = FwhtShape<LOGL>::ROUNDS;
-  return LOGL / R + (rnd < LOGL % R ? 1 : 0);
-}
+struct FwhtRounds {
+  static constexpr int R = FwhtShape<LOGL>::ROUNDS;
+  static constexpr int g(int rnd) { return LOGL / R + (rnd < LOGL % R ? 1 : 0); }
+  static constexpr int lev(int rnd) {
+    int l = 0;
+    for (int i = 0; i < rnd; ++i) l += g(i);
+    return l;
+  }
+};
 
-// One register round: g levels starting at tile-row bit `lev`.  Values come
-// from global memory in the first round and go to global memory in the last.
-template <int LOGL, int G>
-__device__ __forceinline__ void do_round(const FwhtArgs& a, long long* tile, const int32_t* gmap,
-                                         const int32_t* dmap, const int32_t* hmap,
-                                         const int* sh, int lev, bool from_global, bool to_global,
-                                         int c0, int64_t low, int64_t high) {
+// What one thread of k_fwht_pass needs for its column (threads keep one tile
+// column c = tid mod TC for the whole pass).  Global rows of the tile,
+// low | t << shift_lo | high << (shift_lo + LOGL), are low + high 2^(shift_lo + LOGL)
+// plus t 2^shift_lo (the bit fields do not overlap), so a work-buffer element
+// of tile row t sits at wb + t * wst.
+struct PassCol {
+  long long* tc;          // this column of the shared-memory tile
+  bool ok;                // column < C
+  bool isx;               // column < d (a column of X, not Y)
+  int s;                  // fixed-point scale exponent of the column
+  uint32_t nrows;         // N (rows of X and Y; at most 2^30)
+  const char* src;        // first pass: the column's first element
+  uint64_t sstride;       // first pass: bytes between rows of that column
+  long long* wb;          // work buffer, tile row 0 of this column
+  int64_t wst;            // elements between tile rows in the work buffer
+  double* ak;             // last pass: column of A_K (FP64), or null
+  __nv_bfloat16* ak16;    // last pass: column of A_K (BF16), or null
+  double* ahat;           // last pass: column of S-hat X
+};
+
+template <int LOGL, int RND>
+__device__ __forceinline__ void pass_round(const FwhtArgs& a, const PassCol& pc,
+                                           const int32_t* gmap, const int32_t* dmap,
+                                           const int32_t* hmap) {
   using S = FwhtShape<LOGL>;
-  constexpr int L = S::L, TC = S::TC, NT = S::THREADS, GN = 1 << G;
-  const int h = 1 << lev;
-  for (int q = threadIdx.x; q < (L / GN) * TC; q += NT) {
-    const int c = q % TC, gi = q / TC;
-    const int t0 = (gi & (h - 1)) | ((gi >> lev) << (lev + G));
-    const int col = c0 + c;
+  using RS = FwhtRounds<LOGL>;
+  constexpr int L = S::L, TC = S::TC, NT = S::THREADS;
+  constexpr int G = RS::g(RND), LEV = RS::lev(RND), H = 1 << LEV, GN = 1 << G;
+  constexpr bool FROM = (RND == 0), TO = (RND == RS::R - 1);
+  constexpr int NG = L / GN, GS = NT / TC;
+  const int64_t hst = (int64_t)H * pc.wst;
+  for (int gi = threadIdx.x / TC; gi < NG; gi += GS) {
+    const int t0 = (gi & (H - 1)) | ((gi >> LEV) << (LEV + G));
     long long v[GN];
-    if (from_global) {
-      // All GN loads are issued before any is used: addresses are clamped to
-      // valid memory and the values masked afterwards, so no load waits
-      // behind a branch.
-      const bool colok = col < a.C;
-      const int colc = colok ? col : 0;
+    if constexpr (FROM) {
       if (a.first) {
-        double raw[GN];
+        // All GN loads are issued before any is used: rows past N read row 0
+        // and are zeroed afterwards, so no load waits behind a branch.  The
+        // sign of D is applied to the FP64 sign bit before the conversion
+        // (which rounds the magnitude), the same as negating its result.
         uint32_t gm[GN];
+        double raw[GN];
 #pragma unroll
         for (int k = 0; k < GN; ++k) {
-          gm[k] = (uint32_t)gmap[t0 + k * h];
-          const int64_t src = (int64_t)(gm[k] & 0x7FFFFFFFu);
-          const int64_t srcc = src < a.N ? src : 0;
-          const double* ptr = (colc < a.d) ? a.X + srcc * a.ldx + colc : a.Y + srcc;
-          raw[k] = __ldg(ptr);
+          gm[k] = (uint32_t)gmap[t0 + k * H];
+          const uint32_t src = gm[k] & 0x7FFFFFFFu;
+          const uint32_t srcc = src < pc.nrows ? src : 0u;
+          raw[k] = __ldg(reinterpret_cast<const double*>(pc.src + (uint64_t)srcc * pc.sstride));
         }
 #pragma unroll
         for (int k = 0; k < GN; ++k) {
-          const int64_t src = (int64_t)(gm[k] & 0x7FFFFFFFu);
-          long long x = (colok && src < a.N) ? to_fixed(raw[k], sh[c]) : 0;
-          v[k] = (gm[k] & 0x80000000u) ? -x : x;
+          const bool live = pc.ok && (gm[k] & 0x7FFFFFFFu) < pc.nrows;
+          unsigned long long b = (unsigned long long)__double_as_longlong(raw[k]) ^
+                                 ((unsigned long long)(gm[k] & 0x80000000u) << 32);
+          b = live ? b : 0ull;
+          v[k] = to_fixed(__longlong_as_double((long long)b), pc.s);
         }
       } else {
+        const long long* p = pc.wb + (int64_t)t0 * pc.wst;
 #pragma unroll
-        for (int k = 0; k < GN; ++k) {
-          const int t = t0 + k * h;
-          const int64_t j = low | ((int64_t)t << a.shift_lo) | (high << (a.shift_lo + LOGL));
-          v[k] = a.W[j * a.ldw + colc];
-        }
-        if (!colok)
+        for (int k = 0; k < GN; ++k) v[k] = p[k * hst];
+        if (!pc.ok)
 #pragma unroll
           for (int k = 0; k < GN; ++k) v[k] = 0;
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < GN; ++k) v[k] = tile[(t0 + k * h) * TC + c];
+      for (int k = 0; k < GN; ++k) v[k] = pc.tc[(t0 + k * H) * TC];
     }
     bfly<G>(v);
+    if constexpr (!TO) {
 #pragma unroll
-    for (int k = 0; k < GN; ++k) {
-      const int t = t0 + k * h;
-      if (!to_global) {
-        tile[t * TC + c] = v[k];
-      } else if (col < a.C) {
-        if (!a.last) {
-          const int64_t j = low | ((int64_t)t << a.shift_lo) | (high << (a.shift_lo + LOGL));
-          a.W[j * a.ldw + col] = v[k];
-        } else {
+      for (int k = 0; k < GN; ++k) pc.tc[(t0 + k * H) * TC] = v[k];
+    } else if (pc.ok) {
+      if (!a.last) {
+        long long* p = pc.wb + (int64_t)t0 * pc.wst;
+#pragma unroll
+        for (int k = 0; k < GN; ++k) p[k * hst] = v[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < GN; ++k) {
+          const int t = t0 + k * H;
           const int32_t dst = dmap[t], hd = hmap[t];
           if (dst >= 0 || hd >= 0) {
-            const double z = from_fixed(v[k], sh[c]);
+            const double z = from_fixed(v[k], pc.s);
             if (dst >= 0) {
-              if (col < a.d) {
-                if (a.AK) a.AK[(int64_t)dst * a.ldak + col] = z;
-                if (a.AK16) a.AK16[(int64_t)dst * a.ldak16 + col] = __double2bfloat16(z);
+              if (pc.isx) {
+                if (pc.ak) pc.ak[(int64_t)dst * a.ldak] = z;
+                if (pc.ak16) pc.ak16[(int64_t)dst * a.ldak16] = __double2bfloat16(z);
               } else {
                 a.bK[dst] = z;
               }
             }
-            if (hd >= 0 && col < a.d) a.Ahat[(int64_t)col * a.r + hd] = z * a.hat_scale;
+            if (hd >= 0 && pc.isx) pc.ahat[hd] = z * a.hat_scale;
           }
         }
       }
@@ -258,16 +284,29 @@ __device__ __forceinline__ void do_round(const FwhtArgs& a, long long* tile, con
   }
 }
 
+template <int LOGL, int RND>
+__device__ __forceinline__ void pass_rounds(const FwhtArgs& a, const PassCol& pc,
+                                            const int32_t* gmap, const int32_t* dmap,
+                                            const int32_t* hmap) {
+  if constexpr (RND < FwhtRounds<LOGL>::R) {
+    pass_round<LOGL, RND>(a, pc, gmap, dmap, hmap);
+    if constexpr (RND + 1 < FwhtRounds<LOGL>::R) {
+      __syncthreads();
+      pass_rounds<LOGL, RND + 1>(a, pc, gmap, dmap, hmap);
+    }
+  }
+}
+
 template <int LOGL>
 __global__ void __launch_bounds__(512) k_fwht_pass(const FwhtArgs a) {
   using S = FwhtShape<LOGL>;
-  constexpr int L = S::L, TC = S::TC, NT = S::THREADS, R = S::ROUNDS;
+  constexpr int L = S::L, TC = S::TC, NT = S::THREADS;
+  static_assert(NT % TC == 0, "a thread keeps one column");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* tile = reinterpret_cast<long long*>(smem_raw);
   int32_t* gmap = reinterpret_cast<int32_t*>(tile + (size_t)L * TC);
   int32_t* dmap = gmap + L;
   int32_t* hmap = dmap + L;
-  int* sh = hmap + L;
 
   const int64_t blk = blockIdx.x;
   const int ct = (int)(blk % a.ncoltiles);
@@ -275,34 +314,34 @@ __global__ void __launch_bounds__(512) k_fwht_pass(const FwhtArgs a) {
   const int c0 = ct * TC;
   const int64_t low = base & ((int64_t(1) << a.shift_lo) - 1);
   const int64_t high = base >> a.shift_lo;
-  auto grow = [&](int t) -> int64_t {
-    return low | ((int64_t)t << a.shift_lo) | (high << (a.shift_lo + LOGL));
-  };
   const int tid = threadIdx.x;
-  for (int c = tid; c < TC; c += NT) sh[c] = (c0 + c < a.C) ? a.shift[c0 + c] : 0;
   if (a.first)
-    for (int t = tid; t < L; t += NT) gmap[t] = (int32_t)a.gather[grow(t)];
+    for (int t = tid; t < L; t += NT)
+      gmap[t] = (int32_t)a.gather[low | ((int64_t)t << a.shift_lo) | (high << (a.shift_lo + LOGL))];
   if (a.last)   // the maps are stored in the last pass's row order
     for (int t = tid; t < L; t += NT) {
       dmap[t] = a.dest[base * L + t];
       hmap[t] = a.hdest[base * L + t];
     }
-  __syncthreads();
 
-  int lev = 0;
-#pragma unroll 1
-  for (int rnd = 0; rnd < R; ++rnd) {
-    const int g = round_levels<LOGL>(rnd);
-    const bool fg = (rnd == 0), tg = (rnd == R - 1);
-    switch (g) {
-      case 1: do_round<LOGL, 1>(a, tile, gmap, dmap, hmap, sh, lev, fg, tg, c0, low, high); break;
-      case 2: do_round<LOGL, 2>(a, tile, gmap, dmap, hmap, sh, lev, fg, tg, c0, low, high); break;
-      case 3: do_round<LOGL, 3>(a, tile, gmap, dmap, hmap, sh, lev, fg, tg, c0, low, high); break;
-      default: do_round<LOGL, 4>(a, tile, gmap, dmap, hmap, sh, lev, fg, tg, c0, low, high); break;
-    }
-    lev += g;
-    __syncthreads();
-  }
+  PassCol pc;
+  const int c = tid % TC;
+  const int col = c0 + c;
+  pc.tc = tile + c;
+  pc.ok = col < a.C;
+  const int colc = pc.ok ? col : 0;   // a valid column for the masked loads
+  pc.isx = colc < a.d;
+  pc.s = a.shift[colc];
+  pc.nrows = (uint32_t)a.N;
+  pc.src = pc.isx ? reinterpret_cast<const char*>(a.X + colc) : reinterpret_cast<const char*>(a.Y);
+  pc.sstride = pc.isx ? (uint64_t)a.ldx * sizeof(double) : sizeof(double);
+  pc.wst = a.ldw << a.shift_lo;
+  pc.wb = a.W ? a.W + (low + (high << (a.shift_lo + LOGL))) * a.ldw + colc : nullptr;
+  pc.ak = a.AK ? a.AK + colc : nullptr;
+  pc.ak16 = a.AK16 ? a.AK16 + colc : nullptr;
+  pc.ahat = a.Ahat ? a.Ahat + (int64_t)colc * a.r : nullptr;
+  __syncthreads();
+  pass_rounds<LOGL, 0>(a, pc, gmap, dmap, hmap);
 }
 
 // ---------------------------------------------------------------------------
@@ -511,11 +550,19 @@ static spcg_status launch_logl(int logl, const FwhtArgs& a, int64_t nbases, cuda
 }
 
 // Split n index bits into passes of at most 12 bits, as even as possible,
-// the larger passes first; first_levels (> 0) fixes the first pass of a
+// the larger passes first, except that a two-pass plan gives its last pass
+// (the scatter to the nested positions) 9 levels when the first then has at
+// most 11: a 9-level tile takes 70 KB, so two CTAs share an SM and one's
+// loads overlap the other's butterflies (at n = 20, 11 + 9 levels measured
+// faster than 10 + 10).  first_levels (> 0) fixes the first pass of a
 // two-pass plan instead.
 int fwht_pass_plan(int n, int* logl, int first_levels) {
   const int passes = (n + 11) / 12;
   for (int p = 0; p < passes; ++p) logl[p] = n / passes + (p < n % passes ? 1 : 0);
+  if (passes == 2 && logl[1] > 9 && n - 9 <= 11) {
+    logl[0] = n - 9;
+    logl[1] = 9;
+  }
   if (passes == 2 && first_levels > 0 && first_levels <= 12 && n - first_levels >= 1 &&
       n - first_levels <= 12) {
     logl[0] = first_levels;
