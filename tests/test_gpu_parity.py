@@ -210,14 +210,17 @@ def test_sketch_and_stages_with_uneven_stage_sizes():
 # passes must give the same bits; one of them is checked against the oracle's
 # FP64 transform row by row.  N' = 2^19 (ragged N, 33 + 1 columns: partial
 # column tiles), plans 10 + 9 (default), 9 + 10, 12 + 7 (the 7-level pass on
-# the per-round kernel).
+# the per-round kernel), and 11 + 8, 12 + 7, 8 + 11 and 7 + 12 with every
+# pass on the per-round kernel (its 11- and 12-level tiles, 2048 x 8 and
+# 4096 x 4, as the gathering first pass and as the scattering last pass).
 def test_transform_variants_and_plans_are_bit_identical():
     N, d, seed = (1 << 18) + 37, 33, 12
     X, Y, _ = gaussian_problem(N, d, 1.0, seed=seed)
     sched = OS.default_schedule(N, d)
     mK = sched["m"][-1]
     outs = []
-    for tile, first in ((0, 0), (1, 0), (2, 0), (3, 0), (1, 9), (2, 9), (1, 12)):
+    for tile, first in ((0, 0), (1, 0), (2, 0), (3, 0), (1, 9), (2, 9), (1, 12),
+                        (3, 11), (3, 12), (3, 8), (3, 7)):
         o = S.Opts()
         o.fwht_tile = tile
         o.fwht_first_levels = first
