@@ -23,12 +23,13 @@ Counter layout (the CUDA side implements the same definition separately):
       F = word0(philox(ctr=(v, i, tag, n), key=seed))
 
 Parity: the CPU and GPU generators are compared bit for bit (integer work).
-Pins: bijectivity and inverse on exhaustive small domains, bit balance and
+Pins: Philox4x32-10 word for word against an independent implementation of
+the same published generator (Triton's, run by its CPU interpreter; the
+published known-answer vectors themselves are not available offline), which
+fixes the multipliers, Weyl constants, round count, key split and word
+order; bijectivity and inverse on exhaustive small domains, bit balance and
 chi-square uniformity of Philox words, uniform position distribution of the
-permutation over seeds, avalanche of the round function.  Published
-known-answer vectors are not available offline, so the exact Philox
-constants are pinned only through those statistical properties
-("parity unpinned" against the published test vectors).
+permutation over seeds, avalanche of the round function.
 """
 import numpy as np
 
