@@ -235,8 +235,10 @@ spcg_status spcg_tuned_schedule(int64_t N, int32_t d, spcg_schedule* out);
  *   stream cudaStream_t for all work of this context (NULL = default stream).
  *   opts   NULL for defaults.
  *   out    receives the context (set to NULL on failure).
- * Errors: SPCG_E_INVALID_ARG, SPCG_E_OOM (a device allocation failed, or the
- * workspace would pass opts->max_workspace_bytes), SPCG_E_CUDA.
+ * Errors: SPCG_E_INVALID_ARG (a pointer, size or option out of its
+ * documented range; found before any CUDA call), SPCG_E_OOM (a device
+ * allocation failed, or the workspace would pass opts->max_workspace_bytes),
+ * SPCG_E_CUDA.
  */
 spcg_status spcg_create(const double* X, const double* Y, int64_t N, int32_t d,
                         int64_t ldx, void* stream, const spcg_opts* opts,
@@ -337,8 +339,9 @@ spcg_status spcg_solve_result(spcg_ctx* ctx, spcg_info* info);
  * library keeps per device: freed at the end of the call, the memory stays in
  * the pool for the next call (of any size) instead of going back to the
  * device, so repeated calls skip the allocation cost.  spcg_host_pool_trim
- * hands it back.  Synchronises `stream`.  Errors: SPCG_E_INVALID_ARG,
- * SPCG_E_OOM, SPCG_E_CUDA and those of spcg_solve.
+ * hands it back.  Synchronises `stream`.  Errors: SPCG_E_INVALID_ARG (as
+ * spcg_create, found before any CUDA call), SPCG_E_OOM, SPCG_E_CUDA and those
+ * of spcg_solve.
  */
 spcg_status spcg_solve_host(const double* X, const double* Y, int64_t N, int32_t d, int64_t ldx,
                             uint64_t seed, const spcg_schedule* sched, const spcg_opts* opts,

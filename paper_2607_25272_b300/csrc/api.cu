@@ -404,6 +404,14 @@ spcg_status host_pool(int dev, cudaMemPool_t* out) {
 }
 }  // namespace
 
+// Options out of their documented ranges (checked before any CUDA call).
+static bool opts_valid(const spcg_opts& o) {
+  return (o.precision == SPCG_PREC_FP64 || o.precision == SPCG_PREC_MIXED) &&
+         o.fwht_tile >= 0 && o.fwht_tile <= 3 && o.fwht_first_levels >= 0 &&
+         o.fwht_first_levels <= 12 && o.max_workspace_bytes >= 0 && o.qr_panel_ctas >= 0 &&
+         o.dspace_ctas >= 0 && o.qr_by_column >= 0 && o.qr_by_column <= 2;
+}
+
 static spcg_status create_impl(const double* X, const double* Y, int64_t N, int32_t d,
                                int64_t ldx, void* stream, const spcg_opts* opts,
                                cudaMemPool_t pool, spcg_ctx** out) {
@@ -411,6 +419,7 @@ static spcg_status create_impl(const double* X, const double* Y, int64_t N, int3
   *out = nullptr;
   if (!X || !Y || d < 1 || d > SPCG_MAX_D || N <= d || N > (int64_t(1) << 30) || ldx < d)
     return SPCG_E_INVALID_ARG;
+  if (opts && !opts_valid(*opts)) return SPCG_E_INVALID_ARG;
   spcg_ctx* c = new spcg_ctx();
   c->pool = pool;
   c->stream = (cudaStream_t)stream;
@@ -473,13 +482,6 @@ static spcg_status create_impl(const double* X, const double* Y, int64_t N, int3
   if ((st = dalloc(c, &c->feat_part, 2 * 128)) != SPCG_OK) return fail(st);
   if ((st = dalloc(c, &s.colshift, (size_t)d + 1)) != SPCG_OK) return fail(st);
   if ((st = make_pass_geom(c->X, N, d, c->ldx, &c->gx)) != SPCG_OK) return fail(st);
-  if (c->opts.precision != SPCG_PREC_FP64 && c->opts.precision != SPCG_PREC_MIXED)
-    return fail(SPCG_E_INVALID_ARG);
-  if (c->opts.fwht_tile < 0 || c->opts.fwht_tile > 3 || c->opts.fwht_first_levels < 0 ||
-      c->opts.fwht_first_levels > 12 || c->opts.max_workspace_bytes < 0 ||
-      c->opts.qr_panel_ctas < 0 || c->opts.dspace_ctas < 0 || c->opts.qr_by_column < 0 ||
-      c->opts.qr_by_column > 2)
-    return fail(SPCG_E_INVALID_ARG);
   if (c->opts.precision == SPCG_PREC_MIXED) {
     c->ldxf = (d + 3) & ~int64_t(3);
     if ((st = dalloc(c, &c->Xf, (size_t)N * c->ldxf)) != SPCG_OK) return fail(st);
@@ -787,7 +789,7 @@ extern "C" spcg_status spcg_solve_host(const double* X, const double* Y, int64_t
                                        const spcg_opts* opts, void* stream, double* beta,
                                        spcg_info* info) {
   if (!X || !Y || !beta || d < 1 || d > SPCG_MAX_D || N <= d || N > (int64_t(1) << 30) ||
-      ldx < d)
+      ldx < d || (opts && !opts_valid(*opts)))
     return SPCG_E_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;

@@ -92,6 +92,30 @@ def test_invalid_arguments_rejected_before_any_cuda_call():
     L.spcg_destroy(None)   # no-op
 
 
+@pytest.mark.parametrize("field,value", [("precision", 2), ("precision", -1), ("fwht_tile", 4),
+                                         ("fwht_tile", -1), ("fwht_first_levels", 13),
+                                         ("fwht_first_levels", -1), ("max_workspace_bytes", -1),
+                                         ("qr_panel_ctas", -1), ("dspace_ctas", -1),
+                                         ("qr_by_column", 3), ("qr_by_column", -1)])
+def test_options_out_of_range_rejected_before_any_cuda_call(field, value):
+    """Every spcg_opts field outside its documented range gives
+    SPCG_E_INVALID_ARG from spcg_create and spcg_solve_host before any CUDA
+    call (so also on a host without a GPU); the context stays NULL."""
+    L = S.lib()
+    o = S.Opts()
+    setattr(o, field, value)
+    out = ctypes.c_void_p()
+    fake = ctypes.c_void_p(16)
+    assert L.spcg_create(fake, fake, 100, 5, 5, None, ctypes.byref(o),
+                         ctypes.byref(out)) == S.SPCG_E_INVALID_ARG
+    assert out.value is None
+    sch = S.Schedule()
+    assert L.spcg_default_schedule(100, 5, ctypes.byref(sch)) == S.SPCG_OK
+    # X, Y, N, d, ldx, seed, sched, opts, stream, beta, info
+    assert L.spcg_solve_host(fake, fake, 100, 5, 5, ctypes.c_uint64(1), ctypes.byref(sch),
+                             ctypes.byref(o), None, fake, None) == S.SPCG_E_INVALID_ARG
+
+
 def test_struct_layouts_match_header_sizes():
     # spcg_schedule: int32 K, int64 m[40], int32 a[40], int64 r, double tol, 2 x int32
     assert ctypes.sizeof(S.Schedule) == 8 + 8 * 40 + 4 * 40 + 8 + 8 + 8 + 8
