@@ -1015,6 +1015,12 @@ extern "C" spcg_status spcg_batch_create(const spcg_problem_f32* probs, int32_t 
                                          spcg_batch** out) {
   if (!out || !probs || n < 1) return SPCG_E_INVALID_ARG;
   *out = nullptr;
+  for (int i = 0; i < n; ++i) {   // every problem, before any CUDA call
+    const spcg_problem_f32& q = probs[i];
+    if (!q.X || !q.Y || !q.beta || q.d < 1 || q.d > 256 || q.N <= q.d || q.N > (1 << 24) ||
+        q.ldx < q.d || (q.ldx * 4) % 16 != 0 || ((uintptr_t)q.X & 15u) != 0)
+      return SPCG_E_INVALID_ARG;
+  }
   spcg_batch* b = new spcg_batch();
   b->stream = (cudaStream_t)stream;
   b->n = n;
@@ -1022,12 +1028,6 @@ extern "C" spcg_status spcg_batch_create(const spcg_problem_f32* probs, int32_t 
     spcg_batch_destroy(b);
     return s;
   };
-  for (int i = 0; i < n; ++i) {
-    const spcg_problem_f32& q = probs[i];
-    if (!q.X || !q.Y || !q.beta || q.d < 1 || q.d > 256 || q.N <= q.d || q.N > (1 << 24) ||
-        q.ldx < q.d || (q.ldx * 4) % 16 != 0 || ((uintptr_t)q.X & 15u) != 0)
-      return fail(SPCG_E_INVALID_ARG);
-  }
   // solve order: largest N d first (longest-processing-time first)
   b->order.resize(n);
   for (int i = 0; i < n; ++i) b->order[i] = i;

@@ -190,3 +190,70 @@ def test_candidate_schedules_enumerate_the_learned_choice_set(N, d):
         assert list(c2.m[: c2.K]) == paper["m"] and list(c2.a[: c2.K]) == paper["a"]
     with pytest.raises(S.SpcgError):
         S.spcg_candidate_schedule(N, d, 25)
+
+
+def test_batched_and_model_entry_points_reject_bad_arguments():
+    """The batched solver, the schedule model's kernels, the random maps and
+    the context-level calls check their arguments before any CUDA call."""
+    L = S.lib()
+    E = S.SPCG_E_INVALID_ARG
+    a16 = ctypes.c_void_p(1 << 20)            # a 16-byte-aligned stand-in address
+
+    def prob(**kw):
+        q = S.ProblemF32(X=a16, Y=a16, N=1000, d=16, ldx=16, beta=a16)
+        for k, v in kw.items():
+            setattr(q, k, v)
+        return q
+
+    out = ctypes.c_void_p()
+    bad = [dict(d=0), dict(d=257, ldx=260), dict(N=16), dict(N=(1 << 24) + 1), dict(ldx=15),
+           dict(ldx=18), dict(X=ctypes.c_void_p((1 << 20) + 4)), dict(X=None), dict(Y=None),
+           dict(beta=None)]
+    for kw in bad:
+        arr = (S.ProblemF32 * 2)(prob(), prob(**kw))     # the bad one second
+        assert L.spcg_batch_create(arr, 2, None, ctypes.byref(out)) == E, kw
+        assert out.value is None
+        st = (ctypes.c_int32 * 2)()
+        assert L.spcg_solve_batched(arr, 2, 1, 1e-6, None, st, st) == E, kw
+    arr = (S.ProblemF32 * 1)(prob())
+    assert L.spcg_batch_create(arr, 0, None, ctypes.byref(out)) == E
+    assert L.spcg_batch_create(None, 1, None, ctypes.byref(out)) == E
+    assert L.spcg_batch_create(arr, 1, None, None) == E
+    tiles = (ctypes.c_int32 * 4)()
+    assert L.spcg_batch_solve(None, 1, 1e-6, None, None, None) == E
+    assert L.spcg_batch_set_tiles(None, tiles) == E
+    assert L.spcg_batch_autotune(None, 1, 1e-6, tiles) == E
+    assert L.spcg_batch_phase_cycles(None, (ctypes.c_int64 * 8)()) == E
+    L.spcg_batch_destroy(None)   # no-op
+    # schedule model: sizes, output widths, NULL buffers
+    assert L.spcg_num_candidates() == 25
+    assert L.spcg_mlp_params(0) == -1 and L.spcg_mlp_params(1000) == -1
+    assert L.spcg_mlp_params(25) > 0
+    assert L.spcg_mlp_workspace_floats(25, -1) == -1 and L.spcg_mlp_workspace_floats(0, 4) == -1
+    assert L.spcg_mlp_forward(None, 25, a16, 4, a16, None) == E
+    assert L.spcg_mlp_forward(a16, 0, a16, 4, a16, None) == E
+    assert L.spcg_mlp_forward(a16, 25, a16, -1, a16, None) == E
+    assert L.spcg_mlp_forward(a16, 25, a16, 0, a16, None) == S.SPCG_OK       # B = 0: no work
+    assert L.spcg_mlp_grad(a16, 25, a16, a16, 0, a16, a16, a16, None) == E  # B < 1
+    assert L.spcg_mlp_grad(a16, 25, a16, a16, 4, a16, a16, None, None) == E  # no workspace
+    assert L.spcg_mlp_adam(a16, a16, a16, a16, 10, 1e-3, 0, a16, None) == E  # step < 1
+    assert L.spcg_mlp_adam(a16, a16, a16, a16, 0, 1e-3, 1, a16, None) == E   # P < 1
+    assert L.spcg_mlp_to_bf16(None, 10, a16, None) == E
+    # random maps: negative counts, NULL buffers; n = 0 is no work
+    assert L.spcg_philox(None, 1, -1, None, None) == E
+    assert L.spcg_philox(None, 1, 4, a16, None) == E
+    assert L.spcg_philox(None, 1, 0, None, None) == S.SPCG_OK
+    assert L.spcg_signs(1, -1, None, None) == E
+    assert L.spcg_signs(1, 4, None, None) == E
+    assert L.spcg_signs(1, 0, None, None) == S.SPCG_OK
+    # context-level calls with no context or bad sizes
+    info = S.Info()
+    assert L.spcg_refine(None, 1e-6, 10, a16, None) == E
+    assert L.spcg_export_sketch(None, 0, 1, a16, a16) == E
+    assert L.spcg_export_precond(None, a16, a16, a16) == E
+    assert L.spcg_features(None, a16, a16) == E
+    assert L.spcg_solve_enqueue(None, a16, 1, 1) == E
+    assert L.spcg_solve_result(None, ctypes.byref(info)) == E
+    assert L.spcg_solve_learned(None, 1, a16, 25, a16, 1e-6, a16, ctypes.byref(info), None) == E
+    assert L.spcg_solve_candidate(None, 1, 2, 1e-6, 0, a16, ctypes.byref(info)) == E
+    assert L.spcg_solve_candidate(None, 1, 25, 1e-6, 0, a16, ctypes.byref(info)) == E
