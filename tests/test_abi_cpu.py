@@ -257,3 +257,6 @@ def test_batched_and_model_entry_points_reject_bad_arguments():
     assert L.spcg_solve_learned(None, 1, a16, 25, a16, 1e-6, a16, ctypes.byref(info), None) == E
     assert L.spcg_solve_candidate(None, 1, 2, 1e-6, 0, a16, ctypes.byref(info)) == E
     assert L.spcg_solve_candidate(None, 1, 25, 1e-6, 0, a16, ctypes.byref(info)) == E
+    # no spcg_solve_host has run in this process: nothing to trim, no CUDA call
+    assert L.spcg_host_pool_trim() == S.SPCG_OK
+    assert L.spcg_status_str(E) == b"SPCG_E_INVALID_ARG"
