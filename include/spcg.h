@@ -23,6 +23,11 @@
  *   - Device memory is allocated only by spcg_create and spcg_sketch (the
  *     context's workspace) and freed by spcg_destroy.
  *   - A context is not thread-safe; distinct contexts are independent.
+ *   - With SPCG_NVTX=1 in the environment (read once per process) the
+ *     library marks the phases of a solve with NVTX ranges named
+ *     spcg_solve, spcg_sketch, spcg_transform (or spcg_countsketch),
+ *     spcg_precond, "spcg_stage i" and spcg_refine, for a profiler to group
+ *     kernel launches by; without an attached tool the ranges cost nothing.
  */
 #ifndef SPCG_H
 #define SPCG_H
