@@ -78,6 +78,36 @@ def test_exact_preconditioner_converges_in_one_iteration():
     assert rel_pred_error(A, beta, ols(A, b)) < 1e-9
 
 
+def test_pcg_iterates_match_a_library_conjugate_gradient():
+    """The oracle's PCG (CG on the normal equations A^T A beta = A^T b,
+    preconditioned by (R^T R)^{-1}, Sec. 2.2) against scipy's conjugate
+    gradient routine on the same system, preconditioner (formed here as an
+    explicit inverse, not through the oracle's triangular solves) and
+    starting point.  PCG iterates are fixed by those three, so every one of
+    the first eight must agree to rounding; a dropped term, a wrong sign or a
+    stale direction in the recurrence moves them by O(1)."""
+    from scipy.sparse.linalg import LinearOperator, cg
+    rng = np.random.default_rng(5)
+    A, b, _ = svd_problem(600, 12, 1e3, 0.3, seed=7)
+    R = r_factor(A[rng.choice(600, 60, replace=False)])   # an inexact preconditioner
+    beta0 = rng.standard_normal(12)
+    H = A.T @ A
+    Minv = np.linalg.inv(R.T @ R)
+    ref = []
+    cg(LinearOperator((12, 12), matvec=lambda v: H @ v), A.T @ b, x0=beta0, rtol=0.0,
+       atol=0.0, maxiter=8, M=LinearOperator((12, 12), matvec=lambda v: Minv @ v),
+       callback=lambda xk: ref.append(np.array(xk, copy=True)))
+    ours = []
+    pcg(A, b, R, beta0, 8, callback=lambda bt: ours.append(bt.copy()))
+    assert len(ref) == len(ours) == 8
+    x_star = ols(A, b)
+    scale = np.linalg.norm(A @ (beta0 - x_star))
+    for x_ref, x_ours in zip(ref, ours):
+        assert np.linalg.norm(A @ (x_ref - x_ours)) <= 1e-9 * scale
+    # the iterates move: the check is not met by standing still
+    assert np.linalg.norm(A @ (ours[-1] - x_star)) < 1e-3 * scale
+
+
 def test_lemma_a2_cg_bound_each_iterate():
     # ||B(x_j - x*)|| <= 2 ((sqrt k - 1)/(sqrt k + 1))^j ||B(x_0 - x*)|| for
     # B = A R^{-1} (PCG on A = CG on B), kappa = kappa(B^T B) exactly.
