@@ -11,7 +11,10 @@ words): W1 (64 x 4, row-major), b1 (64), W2 (64 x 64), b2 (64),
 W3 (n_out x 64), b3 (n_out).
 
 Pins (tests/test_oracle_mlp.py): the backward pass equals central finite
-differences of the loss; a zero-input network reduces to its biases.
+differences of the loss; a zero-input network reduces to its biases; the
+forward outputs, loss and gradient equal those of the same network built from
+torch's linear layers with automatic differentiation; the BF16 rounding
+equals torch's FP32 -> BF16 conversion.
 """
 import numpy as np
 
