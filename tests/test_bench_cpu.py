@@ -48,3 +48,32 @@ def test_batched_streaming_bound_counts_every_phase():
     b = bench.batch_streaming_bound([(N, d)], [it], 1000.0)
     assert b["alg_bytes"] == want
     assert abs(b["bound_ms"] - want / 1e9) < 1e-12
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the oracle arm, host only) on the small
+    workload: exactly one JSON line on stdout, with the keys of the bench
+    contract, the oracle named as the baseline and no host-device bytes."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "c1", "--steps", "3", "--warmup", "1"],
+                         cwd=ROOT, check=True, capture_output=True, text=True, timeout=600).stdout
+    lines = [ln for ln in out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference"
+    assert line["steps"] == 3 and line["warmup"] == 1 and line["n_gpus"] == 1
+    assert line["higher_is_better"] is False and line["unit"] == "s"
+    assert line["value"] > 0 and abs(line["ms_per_step"] * 3 / 1e3 - line["value"]) < 1e-9
+    assert "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
