@@ -48,3 +48,23 @@ def test_two_ranks_take_max_and_distinct_problems():
         assert p.exitcode == 0
     assert out[0][0] == 11.0 and out[1][0] == 11.0
     assert out[0][1] != out[1][1]
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """`bench.py --impl reference` launched as the bench contract launches it
+    for N > 1 (torchrun, two ranks): rank 0 alone runs the oracle and prints
+    one JSON line; the other rank exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(root, "bench.py"), "--impl", "reference", "--workload", "c1",
+           "--gpus", "2", "--steps", "2", "--warmup", "1"]
+    res = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
