@@ -17,6 +17,18 @@ def test_fwht_equals_explicit_sylvester(n):
     assert np.allclose(fwht_rows(M.copy()), H @ M, rtol=0, atol=1e-13 * np.abs(M).sum())
 
 
+@pytest.mark.parametrize("n", [1, 2, 4, 16, 512])
+def test_sylvester_matrix_and_fwht_match_scipy_hadamard(n):
+    """The oracle's normalised Sylvester matrix equals scipy's Hadamard matrix
+    (Sylvester's construction) divided by sqrt(n), entry for entry, and the
+    fast transform applies that library matrix."""
+    from scipy.linalg import hadamard
+    Hs = hadamard(n).astype(np.float64) / np.sqrt(n)
+    assert np.array_equal(sylvester_matrix(n), Hs)
+    M = np.random.default_rng(n + 1).standard_normal((n, 4))
+    assert np.allclose(fwht_rows(M.copy()), Hs @ M, rtol=0, atol=1e-13 * np.abs(M).sum())
+
+
 def test_sylvester_orthogonal_involution():
     H = sylvester_matrix(256)
     assert np.allclose(H @ H, np.eye(256), atol=1e-13)
