@@ -59,7 +59,7 @@ def test_reference_arm_prints_one_contract_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                           "--workload", "c1", "--steps", "3", "--warmup", "1"],
                          cwd=ROOT, check=True, capture_output=True, text=True, timeout=600).stdout
-    lines = [ln for ln in out.splitlines() if ln.strip()]
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     line = json.loads(lines[0])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
