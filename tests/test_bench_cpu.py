@@ -77,3 +77,18 @@ def test_reference_arm_prints_one_contract_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_bench_accuracy_helpers_agree_with_the_oracle():
+    """The GPU arm's accuracy report uses its own LAPACK least squares (the
+    oracle package runs only in the CPU baseline and the reference arm);
+    on the same problem it agrees with the oracle's OLS estimator and error
+    metric."""
+    from oracle.linalg import ols
+    from oracle.metrics import rel_pred_error
+    X, Y, beta_true = svd_problem(5000, 40, 1e6, 0.1, seed=3)
+    b_lapack = bench.lapack_ols(X, Y)
+    b_oracle = ols(X, Y)
+    assert rel_pred_error(X, b_lapack, b_oracle) <= 1e-9
+    assert abs(bench.rel_error(X, beta_true, b_oracle) - rel_pred_error(X, beta_true, b_oracle)) \
+        <= 1e-12 * rel_pred_error(X, beta_true, b_oracle)
