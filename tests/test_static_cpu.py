@@ -3,6 +3,7 @@ bench.py, __graft_entry__.py or the package's modules reads resolves to a
 module-level name or a builtin.  The GPU-only paths (the timed regions, the
 nested workloads) cannot run on a host without a GPU, so a misspelt or
 removed name there would otherwise surface only on the GPU."""
+import ast
 import builtins
 import dis
 import importlib
@@ -48,4 +49,42 @@ def test_every_global_name_resolves(modname):
         bad = sorted(set(n for n in _globals_read(code) if n not in known))
         if bad:
             missing[fname] = bad
+    assert not missing, missing
+
+
+def _module_aliases(tree):
+    """alias -> module name for every `from X import Y as Z` / `import X as Z`."""
+    out = {}
+    for node in ast.walk(tree):
+        if isinstance(node, ast.ImportFrom) and node.module:
+            for a in node.names:
+                out[a.asname or a.name] = f"{node.module}.{a.name}"
+        elif isinstance(node, ast.Import):
+            for a in node.names:
+                out[a.asname or a.name] = a.name
+    return out
+
+
+@pytest.mark.parametrize("path", ["bench.py", "__graft_entry__.py",
+                                  "paper_2607_25272_b300/schedule_model.py"])
+def test_attributes_of_the_binding_and_oracle_modules_exist(path):
+    """Every `alias.name` read through an imported module of this repository
+    (the binding, the schedule model, the generators, the oracle) names an
+    attribute that module has."""
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    tree = ast.parse(open(os.path.join(root, path)).read())
+    aliases = {k: v for k, v in _module_aliases(tree).items()
+               if v.startswith(("paper_2607_25272_b300.", "oracle."))}
+    missing = []
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Attribute) and isinstance(node.value, ast.Name) \
+                and node.value.id in aliases:
+            modname = aliases[node.value.id]
+            try:
+                mod = importlib.import_module(modname)
+            except ImportError:
+                continue        # a function or class imported by name, not a module
+            if not hasattr(mod, node.attr):
+                missing.append(f"{node.value.id}.{node.attr} (line {node.lineno})")
     assert not missing, missing
