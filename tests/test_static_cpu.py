@@ -88,3 +88,50 @@ def test_attributes_of_the_binding_and_oracle_modules_exist(path):
             if not hasattr(mod, node.attr):
                 missing.append(f"{node.value.id}.{node.attr} (line {node.lineno})")
     assert not missing, missing
+
+
+@pytest.mark.parametrize("path", ["bench.py", "__graft_entry__.py",
+                                  "paper_2607_25272_b300/schedule_model.py"])
+def test_methods_called_on_solver_objects_exist(path):
+    """A name bound to `S.Solver(...)` or `S.Batch(...)` (S the binding
+    module) is only used with attributes that class defines."""
+    import os
+
+    from paper_2607_25272_b300 import spcg as S
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    tree = ast.parse(open(os.path.join(root, path)).read())
+    classes = {"Solver": S.Solver, "Batch": S.Batch}
+    missing, checked = [], 0
+    for fn in ast.walk(tree):
+        if not isinstance(fn, (ast.FunctionDef, ast.Module)):
+            continue
+        bound = {}
+        for node in ast.walk(fn):
+            if isinstance(node, ast.Assign) and isinstance(node.value, ast.Call) \
+                    and isinstance(node.value.func, ast.Attribute) \
+                    and isinstance(node.value.func.value, ast.Name) \
+                    and node.value.func.value.id == "S" and node.value.func.attr in classes:
+                for t in node.targets:
+                    if isinstance(t, ast.Name):
+                        bound[t.id] = classes[node.value.func.attr]
+        for node in ast.walk(fn):
+            if isinstance(node, ast.Attribute) and isinstance(node.value, ast.Name) \
+                    and node.value.id in bound:
+                checked += 1
+                cls = bound[node.value.id]
+                if not hasattr(cls, node.attr) and node.attr not in _instance_attrs(cls):
+                    missing.append(f"{node.value.id}.{node.attr} (line {node.lineno})")
+    assert not missing, missing
+
+
+def _instance_attrs(cls):
+    """Attributes that the class's __init__ assigns on self."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(cls))
+    names = set()
+    for node in ast.walk(ast.parse(src)):
+        if isinstance(node, ast.Attribute) and isinstance(node.value, ast.Name) \
+                and node.value.id == "self" and isinstance(node.ctx, ast.Store):
+            names.add(node.attr)
+    return names
