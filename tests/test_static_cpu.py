@@ -135,3 +135,72 @@ def _instance_attrs(cls):
                 and node.value.id == "self" and isinstance(node.ctx, ast.Store):
             names.add(node.attr)
     return names
+
+
+def _call_shape(call):
+    """(number of positional arguments, keyword names) or None when the call
+    unpacks *args or **kwargs."""
+    if any(isinstance(a, ast.Starred) for a in call.args) or any(k.arg is None for k in call.keywords):
+        return None
+    return len(call.args), [k.arg for k in call.keywords]
+
+
+@pytest.mark.parametrize("path", ["bench.py", "__graft_entry__.py",
+                                  "paper_2607_25272_b300/schedule_model.py"])
+def test_calls_into_the_binding_match_its_signatures(path):
+    """Every call `S.f(...)` of a binding function, `S.Solver(...)`,
+    `S.Batch(...)` and `obj.method(...)` on such objects passes arguments
+    that the Python signature accepts (number of positional arguments and
+    keyword names)."""
+    import inspect
+    import os
+
+    from paper_2607_25272_b300 import spcg as S
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    tree = ast.parse(open(os.path.join(root, path)).read())
+    classes = {"Solver": S.Solver, "Batch": S.Batch}
+    bad, checked = [], 0
+
+    def check(fn, call, skip_self):
+        nonlocal checked
+        shape = _call_shape(call)
+        if shape is None:
+            return
+        try:
+            sig = inspect.signature(fn)
+        except (TypeError, ValueError):
+            return
+        npos, kws = shape
+        args = [None] * (npos + (1 if skip_self else 0))
+        try:
+            sig.bind(*args, **{k: None for k in kws})
+            checked += 1
+        except TypeError as e:
+            bad.append(f"line {call.lineno}: {e}")
+
+    for fn in ast.walk(tree):
+        if not isinstance(fn, ast.FunctionDef):
+            continue
+        bound = {}
+        for node in ast.walk(fn):
+            if isinstance(node, ast.Assign) and isinstance(node.value, ast.Call) \
+                    and isinstance(node.value.func, ast.Attribute) \
+                    and isinstance(node.value.func.value, ast.Name) \
+                    and node.value.func.value.id == "S" and node.value.func.attr in classes:
+                for t in node.targets:
+                    if isinstance(t, ast.Name):
+                        bound[t.id] = classes[node.value.func.attr]
+        for node in ast.walk(fn):
+            if not (isinstance(node, ast.Call) and isinstance(node.func, ast.Attribute)
+                    and isinstance(node.func.value, ast.Name)):
+                continue
+            owner, attr = node.func.value.id, node.func.attr
+            if owner == "S" and hasattr(S, attr) and callable(getattr(S, attr)):
+                target = getattr(S, attr)
+                if isinstance(target, type) and attr in classes:
+                    check(target.__init__, node, skip_self=True)
+                elif inspect.isfunction(target):
+                    check(target, node, skip_self=False)
+            elif owner in bound and inspect.isfunction(getattr(bound[owner], attr, None)):
+                check(getattr(bound[owner], attr), node, skip_self=True)
+    assert not bad, bad
