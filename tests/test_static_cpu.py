@@ -1,8 +1,9 @@
-"""Static check of the host-side Python: every global name that a function of
-bench.py, __graft_entry__.py or the package's modules reads resolves to a
-module-level name or a builtin.  The GPU-only paths (the timed regions, the
-nested workloads) cannot run on a host without a GPU, so a misspelt or
-removed name there would otherwise surface only on the GPU."""
+"""Static checks of the host-side Python: in bench.py, __graft_entry__.py, the
+package's modules and the GPU test modules every global name a function reads
+resolves, every attribute read through an imported module of this repository
+exists, and every call into the binding matches its signature.  The GPU-only
+paths (the timed regions, the nested workloads, the GPU tests) cannot run on
+a host without a GPU, so such a slip would otherwise surface only on the GPU."""
 import ast
 import builtins
 import dis
@@ -11,9 +12,13 @@ import types
 
 import pytest
 
+GPU_TESTS = ["test_gpu_batched", "test_gpu_configs", "test_gpu_learned", "test_gpu_mixed",
+             "test_gpu_parity", "test_gpu_resid", "test_gpu_variants", "test_zz_no_alloc"]
 MODULES = ["bench", "__graft_entry__", "paper_2607_25272_b300.spcg",
            "paper_2607_25272_b300.inputs", "paper_2607_25272_b300.schedule_model",
-           "paper_2607_25272_b300.build"]
+           "paper_2607_25272_b300.build"] + GPU_TESTS
+CALLERS = ["bench.py", "__graft_entry__.py", "paper_2607_25272_b300/schedule_model.py"] + \
+    [f"tests/{m}.py" for m in GPU_TESTS]
 
 
 def _functions(mod):
@@ -65,8 +70,7 @@ def _module_aliases(tree):
     return out
 
 
-@pytest.mark.parametrize("path", ["bench.py", "__graft_entry__.py",
-                                  "paper_2607_25272_b300/schedule_model.py"])
+@pytest.mark.parametrize("path", CALLERS)
 def test_attributes_of_the_binding_and_oracle_modules_exist(path):
     """Every `alias.name` read through an imported module of this repository
     (the binding, the schedule model, the generators, the oracle) names an
@@ -90,8 +94,7 @@ def test_attributes_of_the_binding_and_oracle_modules_exist(path):
     assert not missing, missing
 
 
-@pytest.mark.parametrize("path", ["bench.py", "__graft_entry__.py",
-                                  "paper_2607_25272_b300/schedule_model.py"])
+@pytest.mark.parametrize("path", CALLERS)
 def test_methods_called_on_solver_objects_exist(path):
     """A name bound to `S.Solver(...)` or `S.Batch(...)` (S the binding
     module) is only used with attributes that class defines."""
@@ -145,8 +148,7 @@ def _call_shape(call):
     return len(call.args), [k.arg for k in call.keywords]
 
 
-@pytest.mark.parametrize("path", ["bench.py", "__graft_entry__.py",
-                                  "paper_2607_25272_b300/schedule_model.py"])
+@pytest.mark.parametrize("path", CALLERS)
 def test_calls_into_the_binding_match_its_signatures(path):
     """Every call `S.f(...)` of a binding function, `S.Solver(...)`,
     `S.Batch(...)` and `obj.method(...)` on such objects passes arguments
