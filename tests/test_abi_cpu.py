@@ -260,3 +260,67 @@ def test_batched_and_model_entry_points_reject_bad_arguments():
     # no spcg_solve_host has run in this process: nothing to trim, no CUDA call
     assert L.spcg_host_pool_trim() == S.SPCG_OK
     assert L.spcg_status_str(E) == b"SPCG_E_INVALID_ARG"
+
+
+def _header_prototypes():
+    """name -> (return type, [parameter types]) of every function prototype in
+    include/spcg.h (comments removed; parameter names dropped)."""
+    import re
+    text = open(S.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"([A-Za-z_][A-Za-z_0-9 \*]*?)\b(spcg_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text):
+        ret, name, params = m.group(1).strip(), m.group(2), m.group(3).strip()
+        types = []
+        if params and params != "void":
+            for p in params.split(","):
+                p = " ".join(p.split())
+                ptr = p.count("*")
+                base = re.sub(r"\bconst\b", "", p.replace("*", " "))
+                words = base.split()
+                # drop the parameter name (the last word) when a type precedes it
+                ctype = words[0] if len(words) == 1 else " ".join(words[:-1])
+                types.append((ctype, ptr))
+        protos[name] = (" ".join(ret.split()), types)
+    return protos
+
+
+_SCALARS = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+            "double": ctypes.c_double, "float": ctypes.c_float, "spcg_status": ctypes.c_int,
+            "int": ctypes.c_int}
+
+
+def test_binding_argument_types_match_the_header_prototypes():
+    """Every binding signature has as many arguments as the header's prototype,
+    a pointer where the header has a pointer and the same scalar type where it
+    has a scalar, and a matching return type."""
+    protos = _header_prototypes()
+    assert set(protos) == set(S._SIGS)
+    bad = []
+    for name, (res, args) in S._SIGS.items():
+        ret, params = protos[name]
+        if len(params) != len(args):
+            bad.append(f"{name}: {len(args)} arguments in the binding, {len(params)} in the header")
+            continue
+        for i, ((ctype, ptr), a) in enumerate(zip(params, args)):
+            is_ptr = a is ctypes.c_void_p or a is ctypes.c_char_p or \
+                isinstance(a, type) and issubclass(a, ctypes._Pointer)
+            if ptr:
+                if not is_ptr:
+                    bad.append(f"{name} arg {i}: header {ctype} *, binding {a}")
+            elif ctype in _SCALARS:
+                if a is not _SCALARS[ctype]:
+                    bad.append(f"{name} arg {i}: header {ctype}, binding {a}")
+            else:
+                bad.append(f"{name} arg {i}: unknown header type {ctype}")
+        rptr = ret.count("*")
+        rbase = ret.replace("*", " ").replace("const", " ").split()[-1]
+        if rbase == "void" and not rptr:
+            ok = res is None
+        elif rptr:
+            ok = res in (ctypes.c_void_p, ctypes.c_char_p)
+        else:
+            ok = res is _SCALARS.get(rbase)
+        if not ok:
+            bad.append(f"{name}: return {ret} vs {res}")
+    assert not bad, bad
