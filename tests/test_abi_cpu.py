@@ -324,3 +324,43 @@ def test_binding_argument_types_match_the_header_prototypes():
         if not ok:
             bad.append(f"{name}: return {ret} vs {res}")
     assert not bad, bad
+
+
+def test_a_c_program_links_and_calls_the_library(tmp_path):
+    """The C ABI from C: a program built with gcc against include/spcg.h and
+    linked to libspcg.so calls the host-only entry points (schedule, status
+    string, argument errors) and gets the same answers as the binding."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "caller.c"
+    src.write_text("""
+#include <stdio.h>
+#include "spcg.h"
+int main(void) {
+  spcg_schedule s;
+  if (spcg_default_schedule((int64_t)1 << 20, 500, &s) != SPCG_OK) return 1;
+  printf("K %d r %lld m0 %lld mK %lld a0 %d\\n", s.K, (long long)s.r, (long long)s.m[0],
+         (long long)s.m[s.K - 1], s.a[0]);
+  spcg_ctx* c = (spcg_ctx*)0x1;
+  const int st = (int)spcg_create(NULL, NULL, 100, 5, 5, NULL, NULL, &c);
+  printf("create %d null %d\\n", st, c == NULL);
+  printf("str %s\\n", spcg_status_str(SPCG_E_BREAKDOWN));
+  spcg_destroy(NULL);
+  return 0;
+}
+""")
+    libdir = os.path.dirname(S.LIB_PATH)
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    exe = tmp_path / "caller"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe),
+                    "-L", libdir, "-lspcg", f"-Wl,-rpath,{libdir}"], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    got = dict(zip(out[0::2], out[1::2]))
+    sch = S.spcg_default_schedule(1 << 20, 500)
+    assert int(got["K"]) == sch.K and int(got["r"]) == sch.r
+    assert int(got["m0"]) == sch.m[0] and int(got["mK"]) == sch.m[sch.K - 1]
+    assert int(got["a0"]) == sch.a[0]
+    assert int(got["create"]) == S.SPCG_E_INVALID_ARG and got["null"] == "1"
+    assert got["str"] == "SPCG_E_BREAKDOWN"
