@@ -548,7 +548,7 @@ spcg_status spcg_batch_set_tiles(spcg_batch* b, const int32_t* chunk_bytes4);
  * and keeps the fastest; chosen4 (host, may be NULL) receives the choice. */
 spcg_status spcg_batch_autotune(spcg_batch* b, uint64_t seed, double tol, int32_t* chosen4);
 
-/* ----- Learned schedule (spec growth line; Sec. 4.3 leaves the
+/* ----- Learned schedule (Sec. 4.3 leaves the
  * automatic choice of the sketch-size schedule open) ----- */
 
 /* Number of candidate schedules the model scores (25). */
