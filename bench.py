@@ -55,6 +55,7 @@ WORKLOADS = {
 }
 WARM_SAMPLE_ROWS = 1 << 14    # oracle warm-up sample of the reference arm
 NOMINAL_FP64_TFLOPS = 1.25    # B300 FP64, nominal (context only)
+NOMINAL_HBM_GBS = 7700.0      # B300 HBM3e, nominal (context only; the roofline uses the measured copy)
 # DRAM bytes per algorithmic byte of k_pass (FP64), from the ncu capture of
 # this kernel on a 262144 x 500 operand: read 1.048634624 GB + wrote
 # 2.704384 MB for 1.048576 GB of rows.  Set to None whenever the kernel changes
@@ -150,6 +151,7 @@ def pass_roofline(info, op, peak_gbs, peak_source, traffic_ratio, kernel):
     gbs = per_launch / (ms / n / 1e3) / 1e9
     return {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": peak_gbs, "unit": "GB/s",
             "frac": gbs / peak_gbs, "peak_source": peak_source,
+            "peak_nominal_gbs": NOMINAL_HBM_GBS, "frac_of_nominal": gbs / NOMINAL_HBM_GBS,
             "traffic": per_launch * traffic_ratio if traffic_ratio else None,
             "launches_per_step": n, "alg_bytes_per_launch": per_launch}
 
@@ -926,7 +928,8 @@ def run_ours(args, w, rank, world, local_rank):
                 # (traffic grows with the rows read); None once the kernel changes.
                 "traffic": bytes_per_launch * K_PASS_TRAFFIC_RATIO if K_PASS_TRAFFIC_RATIO else None,
                 "hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak_gbs, "hbm_frac": hbm_gbs / hbm_peak_gbs,
-                "hbm_peak_source": hbm_src,
+                "hbm_peak_source": hbm_src, "hbm_peak_nominal_gbs": NOMINAL_HBM_GBS,
+                "hbm_frac_of_nominal": hbm_gbs / NOMINAL_HBM_GBS,
                 "pass_launches_per_step": pass_n / args.steps,
                 "alg_bytes_per_launch": bytes_per_launch}
     last = infos[-1]

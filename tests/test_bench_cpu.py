@@ -92,3 +92,24 @@ def test_bench_accuracy_helpers_agree_with_the_oracle():
     assert rel_pred_error(X, b_lapack, b_oracle) <= 1e-9
     assert abs(bench.rel_error(X, beta_true, b_oracle) - rel_pred_error(X, beta_true, b_oracle)) \
         <= 1e-12 * rel_pred_error(X, beta_true, b_oracle)
+
+
+def test_pass_roofline_arithmetic():
+    """The HBM roofline of a pass kind from a profiled solve's counters:
+    algorithmic bytes per launch over the mean event time per launch, against
+    the measured peak and, for context, the nominal 7.7 TB/s."""
+    from types import SimpleNamespace
+
+    from paper_2607_25272_b300 import spcg as S
+    k = S.OP_NAMES.index("float32")
+    launches, ms, nbytes = [0] * 4, [0.0] * 4, [0] * 4
+    launches[k], ms[k], nbytes[k] = 10, 5.0, 10 * 3_000_000_000    # 3 GB in 0.5 ms each
+    info = SimpleNamespace(launches_by_op=launches, pass_ms_by_op=ms, bytes_by_op=nbytes)
+    r = bench.pass_roofline(info, "float32", 6000.0, "test peak", 1.01, "k_pass<float>")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 6000.0) < 1e-9 and abs(r["frac"] - 1.0) < 1e-12
+    assert abs(r["frac_of_nominal"] - 6000.0 / 7700.0) < 1e-12
+    assert abs(r["traffic"] - 3.03e9) < 1.0 and r["alg_bytes_per_launch"] == 3e9
+    assert r["launches_per_step"] == 10
+    other = S.OP_NAMES.index("float64")
+    assert bench.pass_roofline(info, S.OP_NAMES[other], 6000.0, "x", None, "k") is None
