@@ -583,15 +583,21 @@ def phase_groups(phases, K):
 
 def cpu_baseline(w, X=None, Y=None):
     """One complete oracle SPCG solve (numpy FP64) of the whole workload at
-    its stated size, wall time, no scaling."""
+    its stated size, wall time, no scaling; beside it, timed separately, the
+    oracle's direct OLS solve (Householder QR) of the same problem."""
+    from oracle.linalg import ols
     from oracle.spcg import spcg as oracle_spcg
     if X is None:
         X, Y, _ = make_problem(w)
     t0 = time.perf_counter()
     oracle_spcg(X, Y, seed=w["seed"], tol=w["tol"])
     sec = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ols(X, Y)
+    ols_sec = time.perf_counter() - t0
     threads = host_threads()
     return {"value": float(sec), "unit": "s", "cores": int(threads), "kind": "oracle",
+            "ols_seconds": float(ols_sec),
             "sample": f"one complete oracle SPCG solve of the whole workload (N={X.shape[0]}, "
                       f"d={X.shape[1]}, same recipe, schedule rule and tol), numpy FP64 with "
                       f"BLAS on {threads} threads (numpy's elementwise transform runs on one); "

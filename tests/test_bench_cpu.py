@@ -113,3 +113,11 @@ def test_pass_roofline_arithmetic():
     assert r["launches_per_step"] == 10
     other = S.OP_NAMES.index("float64")
     assert bench.pass_roofline(info, S.OP_NAMES[other], 6000.0, "x", None, "k") is None
+
+
+def test_cpu_baseline_on_the_small_workload():
+    """The CPU baseline leg on the small workload: one oracle solve timed at
+    full size, the direct OLS solve timed beside it, cores stated."""
+    b = bench.cpu_baseline(bench.WORKLOADS["c1"])
+    assert b["kind"] == "oracle" and b["unit"] == "s" and b["cores"] >= 1
+    assert b["value"] > 0 and b["ols_seconds"] > 0 and b["sample"]
